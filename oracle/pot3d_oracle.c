@@ -1,0 +1,514 @@
+/*
+ * Plain FP64 CPU oracle for the POT3D potential-field solve (arXiv:1709.01126).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The GPU
+ * library shares no code, header, table or constant generator with this file.
+ *
+ * Everything here is written for a reader checking it against the paper:
+ * each step is a separate loop, written in the order the method states it,
+ * with no fusion or blocking.  OpenMP only splits loops over points; every
+ * reduction is combined in a fixed order (per-thread partials summed in
+ * thread order), so results are deterministic for a given thread count.
+ *
+ * Discretisation (Sec. 2.1 Eqs. 1-3, Sec. 2.2 stencil, Eq. 4):
+ *   - Phi is cell-centred in r, theta and phi: unknowns Phi[i][j][k],
+ *     i<nr, j<nt, k<np, stored in C order with phi fastest.
+ *   - The operator is the finite-volume form of the spherical Laplacian,
+ *     multiplied by the cell volume r_i^2 dr_i sin(th_j) dth_j dphi and
+ *     negated, which makes it symmetric positive definite:
+ *        (L x)_c = sum over faces f of c_f * (x_c - x_nb(f))
+ *     with face coefficients
+ *        c^r  (face r_{i+1/2})  = r_{i+1/2}^2 sin(th_j) dth_j dphi / (r_{i+1}-r_i)
+ *        c^th (face th_{j+1/2}) = dr_i sin(th_{j+1/2}) dphi / (th_{j+1}-th_j)
+ *        c^ph (both phi faces)  = dr_i dth_j / (sin(th_j) dphi)
+ *     The paper's printed stencil omits the r^2 and 1/r^2 metric factors;
+ *     this file restores them (the only reading that is symmetric, as
+ *     Sec. 2.3 says A is).
+ *   - Inner boundary r=R_sun (Eq. 2): dPhi/dr = Br is a prescribed flux; the
+ *     face carries no coupling and moves to the right-hand side
+ *        b_c = -r_{1/2}^2 sin(th_j) dth_j dphi Br[j][k]   (i = 0 only).
+ *   - Outer boundary r=R_1, source surface Phi=0 (Sec. 2.1): mirror ghost
+ *     Phi_ghost = -Phi_c at spacing 2 (R_1 - r_last), i.e. a coupling
+ *     2 c^r_outer x_c on the last radial layer.
+ *   - Poles (Eq. 3): the pole faces have sin(0) = sin(pi) = 0 area, so they
+ *     carry no coupling in L; Eq. 3 enters through the field evaluation,
+ *     where the ghost cell across the pole is set so that the face value is
+ *     the phi-average of the first ring (half a cell from the pole).
+ *   - phi is periodic: k-1 and k+1 wrap modulo np.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* status codes returned by orc_pcg */
+#define ORC_OK 0
+#define ORC_NOT_CONVERGED 1
+#define ORC_BREAKDOWN 2
+#define ORC_BAD_ARG 3
+
+typedef struct {
+  int nr, nt, np;
+  double dphi;
+  double *rf, *rc, *dr; /* r faces [nr+1], centres [nr], widths [nr]    */
+  double *tf, *tc, *dt; /* th faces [nt+1], centres [nt], widths [nt]   */
+  double *cr;           /* c^r on face r_{i+1/2}, i = 0..nr-1 (last = outer face) : [nr*nt] */
+  double *ct;           /* c^th on face th_{j+1/2}, j = 0..nt-2 : [nr*(nt-1)]               */
+  double *cp;           /* c^ph : [nr*nt]                                                      */
+  double *diag;         /* diagonal of L : [nr*nt] (independent of k)                          */
+} orc_op;
+
+static int g_threads = 0;
+
+void orc_set_threads(int n) {
+  g_threads = n;
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Radial faces from r0 to r1.  ratio == 1: uniform.  Otherwise geometric:
+ * cell widths dr_i = dr_1 ratio^(i-1) summing to r1 - r0 (Sec. 2.2:
+ * the grid is nonuniform in r). */
+int orc_r_faces(int nr, double r0, double r1, double ratio, double *rf) {
+  if (nr < 1 || !(r1 > r0) || !(ratio > 0)) return ORC_BAD_ARG;
+  if (ratio == 1.0) {
+    for (int i = 0; i <= nr; i++) rf[i] = r0 + (r1 - r0) * (double)i / (double)nr;
+  } else {
+    double dr1 = (r1 - r0) * (ratio - 1.0) / (pow(ratio, (double)nr) - 1.0);
+    for (int i = 0; i <= nr; i++) rf[i] = r0 + dr1 * (pow(ratio, (double)i) - 1.0) / (ratio - 1.0);
+  }
+  rf[0] = r0;
+  rf[nr] = r1;
+  return ORC_OK;
+}
+
+/* Uniform theta faces j*pi/nt, j = 0..nt. */
+int orc_t_faces(int nt, double *tf) {
+  if (nt < 1) return ORC_BAD_ARG;
+  for (int j = 0; j <= nt; j++) tf[j] = ORC_PI * (double)j / (double)nt;
+  tf[0] = 0.0;
+  tf[nt] = ORC_PI;
+  return ORC_OK;
+}
+
+static void op_free(orc_op *op) {
+  free(op->rf); free(op->rc); free(op->dr);
+  free(op->tf); free(op->tc); free(op->dt);
+  free(op->cr); free(op->ct); free(op->cp); free(op->diag);
+}
+
+/* sin of a theta face; the two pole faces are exactly zero (Eq. 3 reading:
+ * the pole face has no area). */
+static double sin_face(const orc_op *op, int jf) {
+  if (jf == 0 || jf == op->nt) return 0.0;
+  return sin(op->tf[jf]);
+}
+
+static int op_build(orc_op *op, int nr, int nt, int np, const double *rf, const double *tf) {
+  memset(op, 0, sizeof(*op));
+  if (nr < 1 || nt < 2 || np < 2) return ORC_BAD_ARG;
+  op->nr = nr; op->nt = nt; op->np = np;
+  op->dphi = 2.0 * ORC_PI / (double)np;
+  op->rf = malloc(sizeof(double) * (nr + 1));
+  op->rc = malloc(sizeof(double) * nr);
+  op->dr = malloc(sizeof(double) * nr);
+  op->tf = malloc(sizeof(double) * (nt + 1));
+  op->tc = malloc(sizeof(double) * nt);
+  op->dt = malloc(sizeof(double) * nt);
+  op->cr = malloc(sizeof(double) * nr * nt);
+  op->ct = malloc(sizeof(double) * nr * (nt > 1 ? nt - 1 : 1));
+  op->cp = malloc(sizeof(double) * nr * nt);
+  op->diag = malloc(sizeof(double) * nr * nt);
+  if (!op->rf || !op->rc || !op->dr || !op->tf || !op->tc || !op->dt || !op->cr || !op->ct ||
+      !op->cp || !op->diag) {
+    op_free(op);
+    return ORC_BAD_ARG;
+  }
+  memcpy(op->rf, rf, sizeof(double) * (nr + 1));
+  memcpy(op->tf, tf, sizeof(double) * (nt + 1));
+  for (int i = 0; i < nr; i++) {
+    op->rc[i] = 0.5 * (rf[i] + rf[i + 1]);
+    op->dr[i] = rf[i + 1] - rf[i];
+  }
+  for (int j = 0; j < nt; j++) {
+    op->tc[j] = 0.5 * (tf[j] + tf[j + 1]);
+    op->dt[j] = tf[j + 1] - tf[j];
+  }
+  const double dphi = op->dphi;
+  for (int i = 0; i < nr; i++) {
+    for (int j = 0; j < nt; j++) {
+      /* radial face r_{i+1/2}: between centres i and i+1, or (outer face)
+         between centre nr-1 and its mirror ghost at 2 R_1 - r_{nr-1}. */
+      double rface = rf[i + 1];
+      double spacing = (i < nr - 1) ? (op->rc[i + 1] - op->rc[i]) : 2.0 * (rf[nr] - op->rc[nr - 1]);
+      op->cr[i * nt + j] = rface * rface * sin(op->tc[j]) * op->dt[j] * dphi / spacing;
+      op->cp[i * nt + j] = op->dr[i] * op->dt[j] / (sin(op->tc[j]) * dphi);
+    }
+    for (int j = 0; j + 1 < nt; j++) {
+      op->ct[i * (nt - 1) + j] =
+          op->dr[i] * sin_face(op, j + 1) * dphi / (op->tc[j + 1] - op->tc[j]);
+    }
+  }
+  /* diagonal: L applied to a unit vector at c, read back at c */
+  for (int i = 0; i < nr; i++) {
+    for (int j = 0; j < nt; j++) {
+      double d = 0.0;
+      if (i < nr - 1) d += op->cr[i * nt + j];
+      else d += 2.0 * op->cr[i * nt + j];
+      if (i > 0) d += op->cr[(i - 1) * nt + j];
+      if (j < nt - 1) d += op->ct[i * (nt - 1) + j];
+      if (j > 0) d += op->ct[i * (nt - 1) + j - 1];
+      d += 2.0 * op->cp[i * nt + j];
+      op->diag[i * nt + j] = d;
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------ operator */
+
+static void op_apply(const orc_op *op, const double *x, double *y) {
+  const int nr = op->nr, nt = op->nt, np = op->np;
+  const long plane = (long)nt * np;
+#pragma omp parallel for schedule(static)
+  for (long rowid = 0; rowid < (long)nr * nt; rowid++) {
+    int i = (int)(rowid / nt), j = (int)(rowid % nt);
+    const double cr_out = op->cr[i * nt + j];
+    const double cr_in = (i > 0) ? op->cr[(i - 1) * nt + j] : 0.0;
+    const double ct_n = (j < nt - 1) ? op->ct[i * (nt - 1) + j] : 0.0;
+    const double ct_s = (j > 0) ? op->ct[i * (nt - 1) + j - 1] : 0.0;
+    const double cphi = op->cp[i * nt + j];
+    for (int k = 0; k < np; k++) {
+      long c = rowid * np + k;
+      double xc = x[c];
+      double s = 0.0;
+      if (i < nr - 1) s += cr_out * (xc - x[c + plane]);
+      else s += cr_out * (xc - (-xc)); /* source surface: mirror ghost */
+      if (i > 0) s += cr_in * (xc - x[c - plane]);
+      /* i == 0: prescribed-flux face, handled by the right-hand side */
+      if (j < nt - 1) s += ct_n * (xc - x[c + np]);
+      if (j > 0) s += ct_s * (xc - x[c - np]);
+      /* pole faces: zero area, no coupling */
+      int kp = (k + 1) % np, km = (k + np - 1) % np;
+      s += cphi * (xc - x[rowid * np + kp]);
+      s += cphi * (xc - x[rowid * np + km]);
+      y[c] = s;
+    }
+  }
+}
+
+/* ------------------------------------------------------ vector helpers */
+
+static double dot(long n, const double *a, const double *b) {
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  double *part = calloc((size_t)nth, sizeof(double));
+#pragma omp parallel num_threads(nth)
+  {
+    int t = 0, T = 1;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+    T = omp_get_num_threads();
+#endif
+    long lo = n * t / T, hi = n * (t + 1) / T;
+    double s = 0.0;
+    for (long q = lo; q < hi; q++) s += a[q] * b[q];
+    part[t] = s;
+  }
+  double s = 0.0;
+  for (int t = 0; t < nth; t++) s += part[t];
+  free(part);
+  return s;
+}
+
+/* ----------------------------------------------------------- public API */
+
+int orc_apply(int nr, int nt, int np, const double *rf, const double *tf, const double *x,
+              double *y) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  op_apply(&op, x, y);
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* Diagonal of L per (i, j) row; the same for every k. */
+int orc_diag(int nr, int nt, int np, const double *rf, const double *tf, double *d) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  memcpy(d, op.diag, sizeof(double) * nr * nt);
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* Face coefficient tables, exposed for the tests: cr [nr*nt], ct [nr*(nt-1)], cp [nr*nt]. */
+int orc_coeffs(int nr, int nt, int np, const double *rf, const double *tf, double *cr, double *ct,
+               double *cp) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  memcpy(cr, op.cr, sizeof(double) * nr * nt);
+  if (nt > 1) memcpy(ct, op.ct, sizeof(double) * nr * (nt - 1));
+  memcpy(cp, op.cp, sizeof(double) * nr * nt);
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* Right-hand side from the inner-boundary Br map (Eq. 2). */
+int orc_rhs(int nr, int nt, int np, const double *rf, const double *tf, const double *br,
+            double *b) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  long n = (long)nr * nt * np;
+  memset(b, 0, sizeof(double) * n);
+  for (int j = 0; j < nt; j++) {
+    double area = rf[0] * rf[0] * sin(op.tc[j]) * op.dt[j] * op.dphi;
+    for (int k = 0; k < np; k++) b[(long)j * np + k] = -area * br[(long)j * np + k];
+  }
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* Textbook preconditioned conjugate gradient with point-Jacobi (diagonal
+ * scaling) preconditioner, PC1 of Sec. 2.3 (Saad, Iterative Methods,
+ * Algorithm 9.1).  x holds the initial guess when x0_given != 0, else it is
+ * zeroed.  Stops after iteration k when ||r_k||_2 / ||b||_2 <= tol.
+ * relres (optional, length maxit+1) receives ||r_k||/||b|| for k = 0..iters.
+ * Returns ORC_OK, ORC_NOT_CONVERGED (iters == maxit, x = last iterate) or
+ * ORC_BREAKDOWN (p.Ap <= 0 or not finite). */
+int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const double *b,
+            double tol, int maxit, int x0_given, double *x, int *iters, double *relres) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  const long n = (long)nr * nt * np;
+  double *r = malloc(sizeof(double) * n);
+  double *z = malloc(sizeof(double) * n);
+  double *p = malloc(sizeof(double) * n);
+  double *q = malloc(sizeof(double) * n);
+  if (!r || !z || !p || !q) {
+    free(r); free(z); free(p); free(q);
+    op_free(&op);
+    return ORC_BAD_ARG;
+  }
+  /* r_0 = b - L x_0 */
+  if (x0_given) {
+    op_apply(&op, x, q);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) r[c] = b[c] - q[c];
+  } else {
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) { x[c] = 0.0; r[c] = b[c]; }
+  }
+  const double bnorm = sqrt(dot(n, b, b));
+  const int np_ = np;
+  /* z_0 = D^-1 r_0 */
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < n; c++) z[c] = r[c] / op.diag[c / np_];
+  /* p_0 = z_0 */
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < n; c++) p[c] = z[c];
+  double rho = dot(n, r, z);
+  double rn = sqrt(dot(n, r, r));
+  if (relres) relres[0] = (bnorm > 0) ? rn / bnorm : 0.0;
+  int k = 0;
+  int status = ORC_NOT_CONVERGED;
+  if (bnorm == 0.0 || rn / bnorm <= tol) status = ORC_OK;
+  while (status == ORC_NOT_CONVERGED && k < maxit) {
+    k++;
+    /* q = L p */
+    op_apply(&op, p, q);
+    /* sigma = p . q ; alpha = rho / sigma */
+    double sigma = dot(n, p, q);
+    if (!(sigma > 0.0) || !isfinite(sigma)) { status = ORC_BREAKDOWN; break; }
+    double alpha = rho / sigma;
+    /* x = x + alpha p */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) x[c] = x[c] + alpha * p[c];
+    /* r = r - alpha q */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) r[c] = r[c] - alpha * q[c];
+    /* convergence: ||r|| / ||b|| <= tol */
+    rn = sqrt(dot(n, r, r));
+    if (relres) relres[k] = rn / bnorm;
+    if (rn / bnorm <= tol) { status = ORC_OK; break; }
+    /* z = D^-1 r */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) z[c] = r[c] / op.diag[c / np_];
+    /* beta = (r_new . z_new) / (r_old . z_old) */
+    double rho_new = dot(n, r, z);
+    double beta = rho_new / rho;
+    rho = rho_new;
+    /* p = z + beta p */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) p[c] = z[c] + beta * p[c];
+  }
+  *iters = k;
+  free(r); free(z); free(p); free(q);
+  op_free(&op);
+  return status;
+}
+
+/* Pole averages (Eq. 3): mean over phi of the first ring at each radius.
+ * north[i] uses j = 0, south[i] uses j = nt-1. */
+int orc_pole_avg(int nr, int nt, int np, const double *phi, double *north, double *south) {
+  for (int i = 0; i < nr; i++) {
+    double sn = 0.0, ss = 0.0;
+    for (int k = 0; k < np; k++) {
+      sn += phi[((long)i * nt + 0) * np + k];
+      ss += phi[((long)i * nt + (nt - 1)) * np + k];
+    }
+    north[i] = sn / (double)np;
+    south[i] = ss / (double)np;
+  }
+  return ORC_OK;
+}
+
+/* Field B = grad Phi on the staggered faces (Sec. 2.1: B = grad Phi).
+ * Output B is three contiguous blocks:
+ *   Br  [(nr+1) * nt * np]  on r faces  r_{i+1/2}, i = -1..nr-1 (face index 0..nr)
+ *   Bth [nr * (nt+1) * np]  on th faces th_{j+1/2}, j = -1..nt-1 (face index 0..nt)
+ *   Bph [nr * nt * np]      on phi faces between k and k+1 (wrapping)
+ * Ghosts: inner Phi_g = Phi_0 - Br dr1 (so the inner face gets Br exactly);
+ * outer Phi_g = -Phi_last (Phi = 0 on the source surface); across a pole
+ * Phi_g = 2 avg - Phi_ring, so the pole face value is the ring's phi-average
+ * (Eq. 3 with epsilon = half the first cell). */
+int orc_field(int nr, int nt, int np, const double *rf, const double *tf, const double *phi,
+              const double *br, double *B) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  double *north = malloc(sizeof(double) * nr), *south = malloc(sizeof(double) * nr);
+  orc_pole_avg(nr, nt, np, phi, north, south);
+  const long n = (long)nr * nt * np;
+  double *Br = B, *Bt = B + (long)(nr + 1) * nt * np, *Bp = Bt + (long)nr * (nt + 1) * np;
+  (void)n;
+  /* Br on radial faces */
+  for (int f = 0; f <= nr; f++) {
+    for (int j = 0; j < nt; j++) {
+      for (int k = 0; k < np; k++) {
+        long o = ((long)f * nt + j) * np + k;
+        if (f == 0) {
+          /* inner ghost: (Phi_0 - (Phi_0 - Br dr1)) / dr1 = Br */
+          Br[o] = br[(long)j * np + k];
+        } else if (f == nr) {
+          double pl = phi[((long)(nr - 1) * nt + j) * np + k];
+          double ghost = -pl;
+          double spacing = 2.0 * (rf[nr] - op.rc[nr - 1]);
+          Br[o] = (ghost - pl) / spacing;
+        } else {
+          double lo = phi[((long)(f - 1) * nt + j) * np + k];
+          double hi = phi[((long)f * nt + j) * np + k];
+          Br[o] = (hi - lo) / (op.rc[f] - op.rc[f - 1]);
+        }
+      }
+    }
+  }
+  /* Btheta on theta faces */
+  for (int i = 0; i < nr; i++) {
+    for (int f = 0; f <= nt; f++) {
+      for (int k = 0; k < np; k++) {
+        long o = ((long)i * (nt + 1) + f) * np + k;
+        double v;
+        if (f == 0) {
+          double p0 = phi[((long)i * nt + 0) * np + k];
+          double ghost = 2.0 * north[i] - p0;
+          double spacing = 2.0 * (op.tc[0] - tf[0]); /* mirror across theta = 0 */
+          v = (p0 - ghost) / (op.rc[i] * spacing);
+        } else if (f == nt) {
+          double pl = phi[((long)i * nt + nt - 1) * np + k];
+          double ghost = 2.0 * south[i] - pl;
+          double spacing = 2.0 * (tf[nt] - op.tc[nt - 1]); /* mirror across theta = pi */
+          v = (ghost - pl) / (op.rc[i] * spacing);
+        } else {
+          double lo = phi[((long)i * nt + f - 1) * np + k];
+          double hi = phi[((long)i * nt + f) * np + k];
+          v = (hi - lo) / (op.rc[i] * (op.tc[f] - op.tc[f - 1]));
+        }
+        Bt[o] = v;
+      }
+    }
+  }
+  /* Bphi on phi faces between k and k+1 (periodic) */
+  for (int i = 0; i < nr; i++) {
+    for (int j = 0; j < nt; j++) {
+      for (int k = 0; k < np; k++) {
+        long c = ((long)i * nt + j) * np;
+        double lo = phi[c + k], hi = phi[c + (k + 1) % np];
+        Bp[c + k] = (hi - lo) / (op.rc[i] * sin(op.tc[j]) * op.dphi);
+      }
+    }
+  }
+  free(north);
+  free(south);
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* Assembled CSR of L for small grids (row order = unknown order; columns
+ * sorted within a row).  Arrays sized by the caller: rowptr[n+1],
+ * col[7n], val[7n].  Returns nnz, or -1 on a bad argument. */
+long orc_csr(int nr, int nt, int np, const double *rf, const double *tf, long *rowptr, long *col,
+             double *val) {
+  orc_op op;
+  if (op_build(&op, nr, nt, np, rf, tf)) return -1;
+  const long plane = (long)nt * np;
+  long nnz = 0;
+  rowptr[0] = 0;
+  for (int i = 0; i < nr; i++) {
+    for (int j = 0; j < nt; j++) {
+      for (int k = 0; k < np; k++) {
+        long c = ((long)i * nt + j) * np + k;
+        /* gather (column, value) pairs for this row, then sort by column */
+        long cols[8];
+        double vals[8];
+        int m = 0;
+        cols[m] = c; vals[m] = op.diag[i * nt + j]; m++;
+        if (i < nr - 1) { cols[m] = c + plane; vals[m] = -op.cr[i * nt + j]; m++; }
+        if (i > 0) { cols[m] = c - plane; vals[m] = -op.cr[(i - 1) * nt + j]; m++; }
+        if (j < nt - 1) { cols[m] = c + np; vals[m] = -op.ct[i * (nt - 1) + j]; m++; }
+        if (j > 0) { cols[m] = c - np; vals[m] = -op.ct[i * (nt - 1) + j - 1]; m++; }
+        long base = ((long)i * nt + j) * np;
+        long kp = base + (k + 1) % np, km = base + (k + np - 1) % np;
+        /* with np == 2 both phi faces couple to the same neighbour */
+        if (kp == km) {
+          cols[m] = kp; vals[m] = -2.0 * op.cp[i * nt + j]; m++;
+        } else {
+          cols[m] = kp; vals[m] = -op.cp[i * nt + j]; m++;
+          cols[m] = km; vals[m] = -op.cp[i * nt + j]; m++;
+        }
+        /* insertion sort by column */
+        for (int a = 1; a < m; a++) {
+          long cc = cols[a]; double vv = vals[a]; int b = a - 1;
+          while (b >= 0 && cols[b] > cc) { cols[b + 1] = cols[b]; vals[b + 1] = vals[b]; b--; }
+          cols[b + 1] = cc; vals[b + 1] = vv;
+        }
+        for (int a = 0; a < m; a++) { col[nnz] = cols[a]; val[nnz] = vals[a]; nnz++; }
+        rowptr[c + 1] = nnz;
+      }
+    }
+  }
+  op_free(&op);
+  return nnz;
+}
