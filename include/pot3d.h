@@ -1,0 +1,184 @@
+/*
+ * pot3d.h — C ABI of the GB300 potential-field solver (libpot3d.so).
+ *
+ * Solves the finite-difference spherical Laplace equation for a coronal
+ * potential field (arXiv:1709.01126):
+ *   - Sec. 2.1, Eq. 1: Laplace equation for the scalar potential Phi,
+ *     B = grad Phi.
+ *   - Sec. 2.1, Eq. 2: inner boundary dPhi/dr = Br at r = r0 (the photosphere).
+ *   - Sec. 2.1: outer boundary "source surface" Phi = 0 at r = r1; phi periodic.
+ *   - Sec. 2.1, Eq. 3: polar boundary value = phi-average of Phi half a cell
+ *     from the pole.
+ *   - Sec. 2.2 and Eq. 4: second-order 7-point finite-difference operator on
+ *     a logically rectangular grid, nonuniform in r and theta, here in its
+ *     symmetric volume-weighted form (the r^2 metric factors restored).
+ *   - Sec. 2.3: preconditioned conjugate gradient with point-Jacobi /
+ *     diagonal scaling (PC1).
+ *
+ * Grid convention: Phi is cell-centred in r, theta and phi.  Unknowns are
+ * Phi[i][j][k], i < nr (r), j < nt (theta, from the north pole), k < np
+ * (phi), stored densely in C order with k fastest (element (i*nt + j)*np + k).
+ *
+ * Pointers.  Array arguments marked "dev or host" may be device pointers
+ * (cudaMalloc / torch CUDA tensors; no copy) or host pointers (staged
+ * through device memory inside the call; pinned host memory makes those
+ * copies asynchronous).  All GPU work runs on the plan's stream (set with
+ * pot3d_set_stream; default: the legacy default stream).  A call that
+ * returns a result on the host (iteration counts, residuals) synchronises
+ * that stream before returning.
+ *
+ * Errors.  Functions return POT3D_OK (0) or a negative POT3D_ERR_* code;
+ * pot3d_plan returns NULL and records the code for pot3d_last_error().
+ * pot3d_strerror maps a code to a static string.  No call aborts the
+ * process; device-side waits are bounded and report POT3D_ERR_TIMEOUT.
+ *
+ * Threads.  One plan must not be used from two host threads at once.
+ * Different plans are independent.
+ */
+#ifndef POT3D_H
+#define POT3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define POT3D_OK 0
+#define POT3D_ERR_INVALID_ARG (-1)  /* bad dimension, pointer, tolerance or option */
+#define POT3D_ERR_OOM (-2)          /* device or host allocation failed            */
+#define POT3D_ERR_CUDA (-3)         /* a CUDA runtime call failed                  */
+#define POT3D_ERR_NOT_CONVERGED (-4)/* iteration cap reached; phi = last iterate   */
+#define POT3D_ERR_BREAKDOWN (-5)    /* PCG breakdown: p.Ap <= 0 or not finite      */
+#define POT3D_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up          */
+#define POT3D_ERR_UNSUPPORTED (-7)  /* option not implemented                      */
+#define POT3D_ERR_BUSY (-8)         /* batch full / no memory to admit now         */
+
+/* ---- arithmetic of the PCG iteration ------------------------------- */
+#define POT3D_PREC_FP64 0    /* every operation in native FP64                      */
+#define POT3D_PREC_FP64_DF 1 /* FP64-class: vectors as (hi, lo) float pairs, every  */
+                             /* operation in double-float arithmetic on FP32 units  */
+#define POT3D_PREC_MIXED 2   /* FP32 inner PCG inside FP64 iterative refinement     */
+
+/* ---- boundary conditions (Sec. 2.1) ---------------------------------- */
+#define POT3D_OUTER_SOURCE_SURFACE 0 /* Phi = 0 at r = r1                              */
+#define POT3D_OUTER_CLOSED_WALL 1    /* Br = 0 at r = r1: POT3D_ERR_UNSUPPORTED for now */
+#define POT3D_POLE_AVERAGE 0         /* Eq. 3                                          */
+
+typedef struct pot3d_plan pot3d_plan_t;
+
+/* Grid description (Sec. 2.2).  nr >= 2, nt >= 2, np >= 3.
+ * Radial faces: r_faces[nr+1] (host, strictly increasing) if non-NULL, else
+ * from r0 to r1 with cell widths dr_i = dr_1 * r_ratio^(i-1) (r_ratio = 1:
+ * uniform).  Colatitude faces: t_faces[nt+1] (host, 0 .. pi, strictly
+ * increasing) if non-NULL, else uniform j*pi/nt.  phi faces are uniform.
+ * The face arrays are copied; the caller keeps ownership. */
+typedef struct {
+  int nr, nt, np;
+  double r0, r1;
+  double r_ratio;
+  const double *r_faces;
+  const double *t_faces;
+  int precision; /* POT3D_PREC_* */
+} pot3d_grid_t;
+
+typedef struct {
+  int outer; /* POT3D_OUTER_* */
+  int pole;  /* POT3D_POLE_* */
+} pot3d_bc_t;
+
+/* Solver options; zero-initialised fields take the defaults. */
+typedef struct {
+  int max_iters;      /* PCG iteration cap (inner cap for MIXED); 0: 4*(nr+nt+np)*8 */
+  int use_x0;         /* 1: phi holds the initial guess on entry of pot3d_solve      */
+  int chunk;          /* iterations enqueued between host polls; 0: automatic        */
+  int use_graphs;     /* 0: automatic (graphs on), 1: on, -1: off                    */
+  int time_kernels;   /* 1: time every iteration kernel with CUDA events (no graphs) */
+  double inner_tol;   /* MIXED: relative tolerance of each inner FP32 solve (0: 1e-4) */
+  int max_outer;      /* MIXED: refinement cap (0: 30)                               */
+} pot3d_opts_t;
+
+/* Statistics of the last solve on a plan. */
+typedef struct {
+  int status;          /* return code of the last solve                         */
+  int iters;           /* PCG iterations (MIXED: total inner FP32 iterations)   */
+  int outer_iters;     /* MIXED: refinement steps (else 0)                       */
+  double relres;       /* final ||r||/||b||: PCG recurrence residual (FP64, DF)
+                          or the recomputed FP64 residual (MIXED)                */
+  double kernel_ms[4]; /* with time_kernels: summed event time of the matvec     */
+                       /* kernel, the update kernel, and their launch counts     */
+} pot3d_stats_t;
+
+/* Static facts about a plan (for measurement and sizing). */
+typedef struct {
+  long long n;               /* unknowns nr*nt*np                                */
+  int pitch;                 /* padded phi length of the internal vectors        */
+  int tiles_matvec;          /* work items of the matvec kernel                  */
+  int tiles_update;          /* work items of the update kernel                  */
+  size_t workspace_bytes;    /* device workspace a solve needs                   */
+  double bytes_matvec;       /* algorithmic HBM bytes per matvec-kernel launch   */
+  double bytes_update;       /* algorithmic HBM bytes per update-kernel launch   */
+} pot3d_info_t;
+
+/* Builds the mesh, the per-(r,theta) metric and diagonal tables and uploads
+ * them (device memory owned by the plan).  Returns NULL on error
+ * (pot3d_last_error()). */
+pot3d_plan_t *pot3d_plan(const pot3d_grid_t *grid, const pot3d_bc_t *bc);
+
+/* Frees everything the plan owns (not a workspace given by the caller). */
+void pot3d_destroy(pot3d_plan_t *plan);
+
+int pot3d_set_stream(pot3d_plan_t *plan, void *cuda_stream);
+int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *opts);
+int pot3d_get_info(const pot3d_plan_t *plan, pot3d_info_t *info);
+int pot3d_last_stats(const pot3d_plan_t *plan, pot3d_stats_t *stats);
+
+/* Device workspace.  By default the plan allocates it with cudaMalloc at
+ * the first solve.  A caller that manages device memory itself passes a
+ * buffer of at least pot3d_workspace_bytes() bytes, 256-byte aligned; it
+ * stays owned by the caller and must outlive the plan's use of it. */
+size_t pot3d_workspace_bytes(const pot3d_plan_t *plan);
+int pot3d_set_workspace(pot3d_plan_t *plan, void *dev_ptr, size_t bytes);
+
+/* Solves L Phi = b(Br) to ||r||/||b|| <= tol (Sec. 2.3 with PC1; stopping
+ * rule checked after every iteration, x0 = 0 unless opts.use_x0).
+ *   br   [nt*np]      dev or host, read      inner-boundary Br (Eq. 2)
+ *   phi  [nr*nt*np]   dev or host, written   the solution (initial guess
+ *                                            when opts.use_x0)
+ *   iters             host, may be NULL      iterations taken
+ * Returns POT3D_OK, POT3D_ERR_NOT_CONVERGED (phi = last iterate),
+ * POT3D_ERR_BREAKDOWN, or an argument / CUDA error.  The arithmetic is the
+ * plan's precision. */
+int pot3d_solve(pot3d_plan_t *plan, const double *br, double tol, double *phi, int *iters);
+
+/* FP64 iterative refinement around FP32 PCG (any plan precision):
+ * outer_iters / inner_iters (host, may be NULL) receive the refinement
+ * steps and the total inner iterations.  Stops when the FP64 residual
+ * ||b - L phi|| / ||b|| <= tol. */
+int pot3d_solve_mixed(pot3d_plan_t *plan, const double *br, double tol, double *phi,
+                      int *outer_iters, int *inner_iters);
+
+/* Field B = grad Phi on staggered faces (Sec. 2.1; poles by Eq. 3).
+ *   phi [nr*nt*np]    dev or host, read
+ *   br  [nt*np]       dev or host, read; NULL = the Br of the last solve
+ *   B                 dev or host, written: three contiguous blocks
+ *       Br  [(nr+1)*nt*np]   radial faces, inner face first (= input Br)
+ *       Bth [nr*(nt+1)*np]   colatitude faces, north pole face first
+ *       Bph [nr*nt*np]       phi faces between k and k+1 (periodic)   */
+int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double *B);
+
+/* y = L x with the FP64 operator of Eq. 4 (no boundary right-hand side).
+ *   x, y [nr*nt*np]  dev or host.  */
+int pot3d_apply(pot3d_plan_t *plan, const double *x, double *y);
+
+/* FP64 relative residual ||b(Br) - L phi|| / ||b(Br)||. br, phi dev or host. */
+int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, double *relres);
+
+int pot3d_last_error(void);
+const char *pot3d_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POT3D_H */

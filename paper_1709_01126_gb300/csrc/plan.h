@@ -1,0 +1,82 @@
+// Internal plan object shared by the translation units of libpot3d.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kernels.cuh"
+#include "pot3d.h"
+
+namespace pot3d {
+
+enum { AR_F64 = 0, AR_DF = 1, AR_F32 = 2 };
+
+// Matvec tile shape: TJ theta rows (one warp each) x 32*VK phi columns.
+constexpr int kTJ = 8;
+constexpr int kVK = 2;
+constexpr int kUpdThreads = 256;
+constexpr int kAuxThreads = 256;
+
+// Per-arithmetic device state of a plan.
+struct ArithData {
+  void *coef = nullptr; // scaled metric table [6][R] in the arithmetic's type
+  ProbDev *d_prob = nullptr;
+  SolveState *d_state = nullptr;
+  double *part_a = nullptr, *part_b = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_chunk = 0;
+  cudaStream_t graph_stream = nullptr;
+  ProbDev h_prob{};
+  bool ready = false;
+};
+
+struct Plan {
+  int nr = 0, nt = 0, np = 0, pitch = 0, prec = 0;
+  size_t R = 0, n = 0, npad = 0;
+  // host mesh (Sec. 2.2) and tables
+  std::vector<double> rf, tf, rc, tc, drc, dtc;
+  double dphi = 0.0;
+  std::vector<double> c64h, S, irs, its, irc, isd;
+  // device constant tables
+  double *d_c64 = nullptr, *d_S = nullptr, *d_irs = nullptr, *d_its = nullptr, *d_irc = nullptr,
+         *d_isd = nullptr, *d_poles = nullptr;
+  // work decomposition
+  int nJ = 0, nK = 0, ic = 0, nI = 0, tiles_a = 0, rows_b = 0, tiles_b = 0;
+  int2 *d_work_a = nullptr, *d_work_b = nullptr;
+  ArithData ar[3];
+  // workspace (vectors)
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  // reductions outside the iteration
+  int aux_blocks = 0;
+  double *d_part = nullptr;
+  double *d_sums = nullptr;
+  double *h_sums = nullptr;    // pinned [8]
+  SolveState *h_state = nullptr; // pinned
+  double *d_br_last = nullptr;
+  bool have_br = false;
+  double *d_stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaStream_t stream = nullptr, own_stream = nullptr, user_stream = nullptr;
+  pot3d_opts_t opts{};
+  pot3d_stats_t stats{};
+  int nsm = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+int fail(int code);
+int cuda_status(cudaError_t e);
+bool is_device_ptr(const void *p);
+int plan_device_init(Plan *P);
+void plan_free(Plan *P);
+int ensure_arith(Plan *P, int ai);
+size_t workspace_bytes(const Plan *P);
+int ensure_workspace(Plan *P);
+void *ws_vec(const Plan *P, int v, size_t es);
+double *ws_x64(const Plan *P);
+double *ws_r64(const Plan *P);
+int stage(Plan *P, size_t bytes);
+void scaled_table(const Plan *P, std::vector<double> &t);
+
+} // namespace pot3d

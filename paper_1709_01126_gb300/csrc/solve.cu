@@ -1,0 +1,525 @@
+// Device set-up, the PCG driver loop, iterative refinement, field, apply
+// and residual entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "aux_kernels.cuh"
+#include "plan.h"
+
+namespace pot3d {
+
+#define TRY(x)                                                                                     \
+  do {                                                                                             \
+    int rc_ = (x);                                                                                 \
+    if (rc_) return fail(rc_);                                                                     \
+  } while (0)
+#define CTRY(x)                                                                                    \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess) return cuda_status(e_);                                                 \
+  } while (0)
+
+static int aux_grid(const Plan *P, size_t n) {
+  size_t b = (n + kAuxThreads - 1) / kAuxThreads;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)P->aux_blocks));
+}
+
+int plan_device_init(Plan *P) {
+  int dev = 0;
+  CTRY(cudaGetDevice(&dev));
+  CTRY(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CTRY(cudaStreamCreateWithFlags(&P->own_stream, cudaStreamDefault));
+  P->stream = P->own_stream;
+  // matvec tiles: theta x phi columns, then enough i-chunks for ~4 waves of
+  // blocks across the SMs without making chunks shorter than 8 planes
+  P->nJ = (P->nt + kTJ - 1) / kTJ;
+  P->nK = (P->np + 32 * kVK - 1) / (32 * kVK);
+  const int cols = P->nJ * P->nK;
+  int nI = (4 * P->nsm + cols - 1) / cols;
+  nI = std::max(1, std::min(nI, std::max(1, P->nr / 8)));
+  P->ic = (P->nr + nI - 1) / nI;
+  P->nI = (P->nr + P->ic - 1) / P->ic;
+  P->tiles_a = cols * P->nI;
+  P->rows_b = 16;
+  P->tiles_b = (int)((P->R + P->rows_b - 1) / P->rows_b);
+  std::vector<int2> wa(P->tiles_a), wb(P->tiles_b);
+  for (int t = 0; t < P->tiles_a; t++) wa[t] = make_int2(0, t);
+  for (int t = 0; t < P->tiles_b; t++) wb[t] = make_int2(0, t);
+  CTRY(cudaMalloc(&P->d_work_a, sizeof(int2) * wa.size()));
+  CTRY(cudaMalloc(&P->d_work_b, sizeof(int2) * wb.size()));
+  CTRY(cudaMemcpy(P->d_work_a, wa.data(), sizeof(int2) * wa.size(), cudaMemcpyHostToDevice));
+  CTRY(cudaMemcpy(P->d_work_b, wb.data(), sizeof(int2) * wb.size(), cudaMemcpyHostToDevice));
+  auto up = [](double **d, const std::vector<double> &h) -> cudaError_t {
+    cudaError_t e = cudaMalloc((void **)d, sizeof(double) * h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+  };
+  CTRY(up(&P->d_c64, P->c64h));
+  CTRY(up(&P->d_S, P->S));
+  CTRY(up(&P->d_irs, P->irs));
+  CTRY(up(&P->d_its, P->its));
+  CTRY(up(&P->d_irc, P->irc));
+  CTRY(up(&P->d_isd, P->isd));
+  CTRY(cudaMalloc(&P->d_poles, sizeof(double) * 2 * P->nr));
+  CTRY(cudaMalloc(&P->d_br_last, sizeof(double) * P->nt * P->np));
+  P->aux_blocks = 4 * P->nsm;
+  CTRY(cudaMalloc(&P->d_part, sizeof(double) * 2 * P->aux_blocks));
+  CTRY(cudaMalloc(&P->d_sums, sizeof(double) * 8));
+  CTRY(cudaMallocHost(&P->h_sums, sizeof(double) * 8));
+  CTRY(cudaMallocHost(&P->h_state, sizeof(SolveState)));
+  memset(P->h_state, 0, sizeof(SolveState));
+  return POT3D_OK;
+}
+
+void plan_free(Plan *P) {
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  for (auto &A : P->ar) {
+    if (A.graph) cudaGraphExecDestroy(A.graph);
+    cudaFree(A.coef);
+    cudaFree(A.d_prob);
+    cudaFree(A.d_state);
+    cudaFree(A.part_a);
+    cudaFree(A.part_b);
+  }
+  for (auto e : P->ev) cudaEventDestroy(e);
+  cudaFree(P->d_work_a);
+  cudaFree(P->d_work_b);
+  cudaFree(P->d_c64);
+  cudaFree(P->d_S);
+  cudaFree(P->d_irs);
+  cudaFree(P->d_its);
+  cudaFree(P->d_irc);
+  cudaFree(P->d_isd);
+  cudaFree(P->d_poles);
+  cudaFree(P->d_br_last);
+  cudaFree(P->d_part);
+  cudaFree(P->d_sums);
+  cudaFree(P->d_stage);
+  if (P->ws_owned) cudaFree(P->ws);
+  if (P->h_sums) cudaFreeHost(P->h_sums);
+  if (P->h_state) cudaFreeHost(P->h_state);
+  if (P->own_stream) cudaStreamDestroy(P->own_stream);
+  cudaGetLastError();
+  delete P;
+}
+
+// ------------------------------------------------------------- iteration
+template <class A>
+static void launch_matvec(Plan *P, int ai) {
+  k_matvec<A, kTJ, kVK><<<P->tiles_a, dim3(32, kTJ), 0, P->stream>>>(P->ar[ai].d_prob, P->d_work_a,
+                                                                     P->tiles_a);
+}
+template <class A>
+static void launch_update(Plan *P, int ai) {
+  k_update<A, kUpdThreads><<<P->tiles_b, kUpdThreads, 0, P->stream>>>(P->ar[ai].d_prob,
+                                                                       P->d_work_b, P->tiles_b);
+}
+
+static int auto_chunk(const Plan *P, int ai) {
+  double t_it;
+  if (ai == AR_F64) t_it = 13.0 * (double)P->n / 0.45e12; // FP64-unit bound
+  else t_it = (ai == AR_DF ? 72.0 : 36.0) * (double)P->n / 4.0e12;
+  t_it = std::max(t_it, 8e-6);
+  int c = (int)(3e-3 / t_it);
+  return std::max(2, std::min(c, 256));
+}
+
+template <class A>
+static int iterate(Plan *P, int ai) {
+  ArithData &D = P->ar[ai];
+  const bool timing = P->opts.time_kernels != 0;
+  const bool graphs = !timing && P->opts.use_graphs >= 0;
+  const int chunk = P->opts.chunk > 0 ? P->opts.chunk : auto_chunk(P, ai);
+  if (timing && (int)P->ev.size() < 3 * chunk) {
+    for (int u = (int)P->ev.size(); u < 3 * chunk; u++) {
+      cudaEvent_t e;
+      CTRY(cudaEventCreate(&e));
+      P->ev.push_back(e);
+    }
+  }
+  int done_before = 0, last_iter = -1;
+  for (;;) {
+    if (timing) {
+      for (int c = 0; c < chunk; c++) {
+        CTRY(cudaEventRecord(P->ev[3 * c], P->stream));
+        launch_matvec<A>(P, ai);
+        CTRY(cudaEventRecord(P->ev[3 * c + 1], P->stream));
+        launch_update<A>(P, ai);
+        CTRY(cudaEventRecord(P->ev[3 * c + 2], P->stream));
+      }
+    } else if (graphs) {
+      if (!D.graph || D.graph_chunk != chunk) {
+        if (D.graph) cudaGraphExecDestroy(D.graph);
+        D.graph = nullptr;
+        cudaGraph_t g;
+        CTRY(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+        for (int c = 0; c < chunk; c++) {
+          launch_matvec<A>(P, ai);
+          launch_update<A>(P, ai);
+        }
+        CTRY(cudaStreamEndCapture(P->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&D.graph, g, 0);
+        cudaGraphDestroy(g);
+        CTRY(e);
+        D.graph_chunk = chunk;
+      }
+      CTRY(cudaGraphLaunch(D.graph, P->stream));
+    } else {
+      for (int c = 0; c < chunk; c++) {
+        launch_matvec<A>(P, ai);
+        launch_update<A>(P, ai);
+      }
+    }
+    CTRY(cudaGetLastError());
+    CTRY(cudaMemcpyAsync(P->h_state, D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                         P->stream));
+    CTRY(cudaStreamSynchronize(P->stream));
+    if (timing) {
+      // only iterations that did work count (kernels exit early once done)
+      const int real = std::min(chunk, P->h_state->iter - done_before);
+      done_before = P->h_state->iter;
+      for (int c = 0; c < real; c++) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, P->ev[3 * c], P->ev[3 * c + 1]);
+        cudaEventElapsedTime(&b, P->ev[3 * c + 1], P->ev[3 * c + 2]);
+        P->stats.kernel_ms[0] += a;
+        P->stats.kernel_ms[1] += b;
+        P->stats.kernel_ms[2] += 1.0;
+        P->stats.kernel_ms[3] += 1.0;
+      }
+    }
+    if (P->h_state->status != ST_RUNNING) break;
+    // a running solve must advance every chunk; if it does not, the
+    // device state is inconsistent: stop instead of polling forever
+    if (P->h_state->iter <= last_iter) return fail(POT3D_ERR_TIMEOUT);
+    last_iter = P->h_state->iter;
+  }
+  return POT3D_OK;
+}
+
+template <class A>
+static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, void *q) {
+  ArithData &D = P->ar[ai];
+  ProbDev &h = D.h_prob;
+  h = ProbDev{};
+  h.nr = P->nr;
+  h.nt = P->nt;
+  h.np = P->np;
+  h.pitch = P->pitch;
+  h.nJ = P->nJ;
+  h.nK = P->nK;
+  h.ic = P->ic;
+  h.nI = P->nI;
+  h.tiles_a = P->tiles_a;
+  h.rows_b = P->rows_b;
+  h.tiles_b = P->tiles_b;
+  h.plane = (long long)P->nt * P->pitch;
+  h.x = x;
+  h.r = r;
+  h.p0 = p0;
+  h.p1 = p1;
+  h.q = q;
+  h.coef = D.coef;
+  h.part_a = D.part_a;
+  h.part_b = D.part_b;
+  h.st = D.d_state;
+}
+
+static int status_code(int st) {
+  switch (st) {
+  case ST_CONVERGED: return POT3D_OK;
+  case ST_MAXIT: return POT3D_ERR_NOT_CONVERGED;
+  case ST_BREAKDOWN: return POT3D_ERR_BREAKDOWN;
+  default: return POT3D_ERR_CUDA;
+  }
+}
+
+static int default_maxit(const Plan *P) { return 100 * (P->nr + P->nt + P->np); }
+
+// Inputs may be host or device pointers; host arrays are staged through
+// one device buffer [br | phi | B].
+struct Io {
+  const double *br = nullptr;
+  double *phi = nullptr;
+  double *B = nullptr;
+  bool br_host = false, phi_host = false, B_host = false;
+};
+
+static int stage_io(Plan *P, const double *br, double *phi, double *B, bool phi_in, Io &io) {
+  io.br_host = br && !is_device_ptr(br);
+  io.phi_host = phi && !is_device_ptr(phi);
+  io.B_host = B && !is_device_ptr(B);
+  const size_t nb = (size_t)P->nt * P->np;
+  const size_t nB = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
+  size_t need = 0;
+  if (io.br_host) need += nb;
+  if (io.phi_host) need += P->n;
+  if (io.B_host) need += nB;
+  if (need) TRY(stage(P, need * sizeof(double)));
+  size_t off = 0;
+  io.br = br;
+  io.phi = phi;
+  io.B = B;
+  if (io.br_host) {
+    io.br = P->d_stage + off;
+    CTRY(cudaMemcpyAsync((void *)io.br, br, nb * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    off += nb;
+  }
+  if (io.phi_host) {
+    io.phi = P->d_stage + off;
+    if (phi_in)
+      CTRY(cudaMemcpyAsync(io.phi, phi, P->n * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    off += P->n;
+  }
+  if (io.B_host) io.B = P->d_stage + off;
+  return POT3D_OK;
+}
+
+template <class A>
+static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi, int *iters) {
+  TRY(ensure_arith(P, ai));
+  TRY(ensure_workspace(P));
+  const bool x0 = P->opts.use_x0 != 0;
+  Io io;
+  TRY(stage_io(P, br, phi, nullptr, x0, io));
+  const size_t es = sizeof(typename A::st);
+  void *x = ws_vec(P, 0, es), *r = ws_vec(P, 1, es), *p0 = ws_vec(P, 2, es),
+       *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
+  ArithData &D = P->ar[ai];
+  fill_prob<A>(P, ai, x, r, p0, p1, q);
+  cudaStream_t s = P->stream;
+  CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+  CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
+                       cudaMemcpyDeviceToDevice, s));
+  P->have_br = true;
+  CTRY(cudaMemsetAsync(P->ws, 0, 5 * ((P->npad * es + 255) & ~(size_t)255), s));
+  const size_t n0 = (size_t)P->nt * P->np;
+  const int gb = aux_grid(P, n0);
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+                                                   P->d_part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
+  if (x0) {
+    const int g = aux_grid(P, P->n);
+    k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+                                                  P->nt, P->np, 0, (double *)q, P->pitch,
+                                                  P->d_part);
+    k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
+  }
+  const int maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
+  k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums, (double)n0, tol, maxit, x0 ? 1 : 0, 0.0);
+  if (x0) {
+    k_x0_setup<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(
+        (const double *)q, io.phi, P->d_c64, P->nr, P->nt, P->np, P->pitch, D.d_state,
+        (typename A::st *)r, (typename A::st *)x);
+    CTRY(cudaMemsetAsync(q, 0, P->npad * es, s));
+  } else {
+    k_write_rhs<A><<<aux_grid(P, n0), kAuxThreads, 0, s>>>(io.br, P->d_S, P->nt, P->np, P->pitch,
+                                                           D.d_state, (typename A::st *)r);
+  }
+  CTRY(cudaGetLastError());
+  memset(&P->stats, 0, sizeof(P->stats));
+  TRY(iterate<A>(P, ai));
+  k_finish<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, io.phi, 1);
+  CTRY(cudaGetLastError());
+  if (io.phi_host)
+    CTRY(cudaMemcpyAsync(phi, io.phi, P->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  const SolveState &hs = *P->h_state;
+  P->stats.status = status_code(hs.status);
+  P->stats.iters = hs.iter;
+  P->stats.outer_iters = 0;
+  P->stats.relres = hs.relres;
+  if (iters) *iters = hs.iter;
+  return P->stats.status ? fail(P->stats.status) : POT3D_OK;
+}
+
+// FP64 iterative refinement (defect correction) around FP32 PCG.
+static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *outer,
+                       int *inner) {
+  TRY(ensure_arith(P, AR_F32));
+  TRY(ensure_workspace(P));
+  const bool x0 = P->opts.use_x0 != 0;
+  Io io;
+  TRY(stage_io(P, br, phi, nullptr, x0, io));
+  cudaStream_t s = P->stream;
+  ArithData &D = P->ar[AR_F32];
+  void *x = ws_vec(P, 0, 4), *r = ws_vec(P, 1, 4), *p0 = ws_vec(P, 2, 4), *p1 = ws_vec(P, 3, 4),
+       *q = ws_vec(P, 4, 4);
+  double *x64 = ws_x64(P), *r64 = ws_r64(P);
+  fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q);
+  CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+  CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
+                       cudaMemcpyDeviceToDevice, s));
+  P->have_br = true;
+  const size_t v4 = (P->npad * 4 + 255) & ~(size_t)255;
+  CTRY(cudaMemsetAsync(P->ws, 0, 5 * v4, s));
+  CTRY(cudaMemsetAsync(x64, 0, P->npad * 8, s));
+  CTRY(cudaMemsetAsync(r64, 0, P->npad * 8, s));
+  if (x0)
+    k_unpad<<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(io.phi, P->np, x64, P->pitch, P->R, P->np);
+  const size_t n0 = (size_t)P->nt * P->np;
+  const int gb = aux_grid(P, n0);
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+                                                   P->d_part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
+  const int gn = aux_grid(P, P->n);
+  const float *dinv32 = static_cast<const float *>(D.coef); // row 0 of the F32 table
+  const double inner_tol = P->opts.inner_tol > 0 ? P->opts.inner_tol : 1e-4;
+  const int max_outer = P->opts.max_outer > 0 ? P->opts.max_outer : 30;
+  const int inner_maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
+  memset(&P->stats, 0, sizeof(P->stats));
+  int n_outer = 0, n_inner = 0, status = POT3D_OK;
+  double bb = 0.0, prev = INFINITY, relres = INFINITY;
+  for (;;) {
+    k_op64<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.br, P->d_S, P->d_c64, P->nr,
+                                                   P->nt, P->np, 0, r64, P->pitch, P->d_part);
+    k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 2);
+    CTRY(cudaGetLastError());
+    CTRY(cudaMemcpyAsync(P->h_sums, P->d_sums, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    CTRY(cudaStreamSynchronize(s));
+    bb = P->h_sums[0];
+    const double rr = P->h_sums[2];
+    relres = (bb > 0) ? std::sqrt(rr) / std::sqrt(bb) : 0.0;
+    if (!std::isfinite(relres)) {
+      status = POT3D_ERR_BREAKDOWN;
+      break;
+    }
+    if (relres <= tol) break;
+    if (n_outer >= max_outer || !(relres < 0.5 * prev)) {
+      status = POT3D_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = relres;
+    // inner system L d = scale * r64 in FP32
+    const double rms = std::sqrt(rr / (double)P->n);
+    const double scale = std::ldexp(1.0, -std::ilogb(rms));
+    k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->np, P->pitch,
+                                                        scale, (float *)r, P->d_part);
+    k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 4);
+    CTRY(cudaMemsetAsync(x, 0, v4, s));
+    CTRY(cudaMemsetAsync(p0, 0, v4, s));
+    CTRY(cudaMemsetAsync(p1, 0, v4, s));
+    CTRY(cudaMemsetAsync(q, 0, v4, s));
+    k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, (double)P->n, inner_tol, inner_maxit, 0,
+                            1.0);
+    CTRY(cudaGetLastError());
+    TRY(iterate<PF32>(P, AR_F32));
+    const SolveState &hs = *P->h_state;
+    n_inner += hs.iter;
+    if (hs.status == ST_BREAKDOWN && hs.iter == 0) {
+      status = POT3D_ERR_BREAKDOWN;
+      break;
+    }
+    k_refine_update<<<gn, kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, x64, 1.0 / scale);
+    n_outer++;
+  }
+  k_unpad<<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.phi, P->np, P->R, P->np);
+  CTRY(cudaGetLastError());
+  if (io.phi_host)
+    CTRY(cudaMemcpyAsync(phi, io.phi, P->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  P->stats.status = status;
+  P->stats.iters = n_inner;
+  P->stats.outer_iters = n_outer;
+  P->stats.relres = relres;
+  if (outer) *outer = n_outer;
+  if (inner) *inner = n_inner;
+  return status ? fail(status) : POT3D_OK;
+}
+
+} // namespace pot3d
+
+using namespace pot3d;
+
+extern "C" {
+
+int pot3d_solve(pot3d_plan_t *plan, const double *br, double tol, double *phi, int *iters) {
+  if (!plan || !br || !phi || !(tol > 0.0) || !std::isfinite(tol)) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  switch (P->prec) {
+  case POT3D_PREC_FP64: return solve_pcg<PF64>(P, AR_F64, br, tol, phi, iters);
+  case POT3D_PREC_FP64_DF: return solve_pcg<PDF>(P, AR_DF, br, tol, phi, iters);
+  default: {
+    int o = 0, in = 0;
+    int rc = solve_mixed(P, br, tol, phi, &o, &in);
+    if (iters) *iters = in;
+    return rc;
+  }
+  }
+}
+
+int pot3d_solve_mixed(pot3d_plan_t *plan, const double *br, double tol, double *phi,
+                      int *outer_iters, int *inner_iters) {
+  if (!plan || !br || !phi || !(tol > 0.0) || !std::isfinite(tol)) return fail(POT3D_ERR_INVALID_ARG);
+  return solve_mixed(reinterpret_cast<Plan *>(plan), br, tol, phi, outer_iters, inner_iters);
+}
+
+int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double *B) {
+  if (!plan || !phi || !B) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  if (!br && !P->have_br) return fail(POT3D_ERR_INVALID_ARG);
+  Io io;
+  TRY(stage_io(P, br, const_cast<double *>(phi), B, true, io));
+  const double *d_br = br ? io.br : P->d_br_last;
+  cudaStream_t s = P->stream;
+  k_pole_avg<kAuxThreads><<<2 * P->nr, kAuxThreads, 0, s>>>(io.phi, P->nr, P->nt, P->np,
+                                                            P->d_poles);
+  FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd};
+  const size_t tot = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
+  k_field<<<aux_grid(P, tot), kAuxThreads, 0, s>>>(io.phi, d_br, P->d_poles, T, P->nr, P->nt, P->np,
+                                                    io.B);
+  CTRY(cudaGetLastError());
+  if (io.B_host) CTRY(cudaMemcpyAsync(B, io.B, tot * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  return POT3D_OK;
+}
+
+int pot3d_apply(pot3d_plan_t *plan, const double *x, double *y) {
+  if (!plan || !x || !y) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  const bool xh = !is_device_ptr(x), yh = !is_device_ptr(y);
+  size_t need = (xh ? P->n : 0) + (yh ? P->n : 0);
+  if (need) TRY(stage(P, need * sizeof(double)));
+  cudaStream_t s = P->stream;
+  const double *dx = x;
+  double *dy = y;
+  size_t off = 0;
+  if (xh) {
+    dx = P->d_stage;
+    CTRY(cudaMemcpyAsync((void *)dx, x, P->n * sizeof(double), cudaMemcpyHostToDevice, s));
+    off = P->n;
+  }
+  if (yh) dy = P->d_stage + off;
+  const int g = aux_grid(P, P->n);
+  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(dx, P->np, nullptr, P->d_S, P->d_c64, P->nr, P->nt,
+                                                P->np, 1, dy, P->np, P->d_part);
+  CTRY(cudaGetLastError());
+  if (yh) CTRY(cudaMemcpyAsync(y, dy, P->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  return POT3D_OK;
+}
+
+int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, double *relres) {
+  if (!plan || !br || !phi || !relres) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  Io io;
+  TRY(stage_io(P, br, const_cast<double *>(phi), nullptr, true, io));
+  cudaStream_t s = P->stream;
+  const size_t n0 = (size_t)P->nt * P->np;
+  const int gb = aux_grid(P, n0);
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+                                                   P->d_part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
+  const int g = aux_grid(P, P->n);
+  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+                                                P->nt, P->np, 0, nullptr, P->np, P->d_part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
+  CTRY(cudaGetLastError());
+  CTRY(cudaMemcpyAsync(P->h_sums, P->d_sums, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  *relres = P->h_sums[0] > 0 ? std::sqrt(P->h_sums[2]) / std::sqrt(P->h_sums[0]) : 0.0;
+  return POT3D_OK;
+}
+
+} // extern "C"
