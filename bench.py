@@ -1,0 +1,413 @@
+"""Benchmark of the potential-field PCG solve on GB300.
+
+One step = one full solve of the 151 x 301 x 601 problem (geometric r mesh,
+ratio 1.02; flux-balanced dipole + 200-bipole synthetic Br, seed 1709;
+Jacobi PCG to relative residual 1e-10) plus the field B = grad Phi, with
+inputs and outputs resident in HBM.  value = PCG iterations per second over
+the timed steps (all ranks).  Each rank of a multi-GPU launch solves its own
+replica (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|df|mixed]
+    python bench.py --impl reference ...   # the CPU oracle as the reference arm
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("PCG iters/s + HBM GB/s (151×301×601 FP64); solves/s & p99, "
+          "mixed+batched vs FP64")
+SHAPE = (151, 301, 601)
+RATIO = 1.02
+TOL = 1e-10
+SEED = 1709
+DTYPES = {"fp64": "f64", "df": "f32x2", "mixed": "f32+f64"}
+
+
+# ----------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+        return dist
+    return None
+
+
+def reduce_max(x: float, dist, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, dist, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        import torch
+
+        t = torch.zeros(1, device=device)
+        dist.all_reduce(t)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 FMA units: 152 SMs x 2 per clock at the 2070 MHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 FMAs per point of the matvec kernel (p~ and x~ updates, 6-term
+# scaled stencil, sigma term): the algorithmic count, halo work excluded
+FP64_FMA_PER_POINT_MATVEC = 9.0
+
+
+# ------------------------------------------------------------- workloads
+def make_br():
+    import pot3d_synth as syn
+
+    return syn.bipole_br(SHAPE[1], SHAPE[2], seed=SEED)
+
+
+def cpu_baseline(br, iters=60):
+    """The oracle as it stands, on the host cores, for a bounded sample:
+    the first `iters` PCG iterations of the same 151x301x601 solve."""
+    import oracle
+
+    oracle.build()
+    n = os.cpu_count() or 1
+    oracle.set_threads(n)
+    g = oracle.Grid(*SHAPE, ratio=RATIO)
+    b = g.rhs(br)
+    g.pcg(b, 1e-300, maxit=2)  # warm the pages
+    t = time.perf_counter()
+    x, it, st = g.pcg(b, 1e-300, maxit=iters)
+    dt = time.perf_counter() - t
+    return {"value": it / dt, "unit": "iters/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "first %d PCG iterations of the 151x301x601 solve (of ~6000 to 1e-10), "
+                      "FP64, OpenMP" % it, "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    dist = dist_init("gloo")
+    if rank != 0:
+        barrier(dist)
+        return 0
+    br = make_br()
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    g = oracle.Grid(*SHAPE, ratio=RATIO)
+    b = g.rhs(br)
+    per_step = 20
+    for _ in range(args.warmup):
+        g.pcg(b, 1e-300, maxit=per_step)
+    t = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        x, it, st = g.pcg(b, 1e-300, maxit=per_step)
+        total += it
+    dt = time.perf_counter() - t
+    v = total / dt
+    line = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "151x301x601 FP64 Jacobi PCG (oracle on host cores); one "
+                                   "step = %d iterations of the solve" % per_step},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "kind": "oracle",
+                             "cores": oracle.get_threads(),
+                             "sample": "%d PCG iterations per step" % per_step},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    barrier(dist)
+    return 0
+
+
+def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=True):
+    """Times `steps` solves (+ field) of one precision after `warmup` solves."""
+    ws, rank, local = dist_env()
+    plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=prec, time_kernels=1)
+    info = plan.info()
+    phi = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
+    B = torch.empty(sum(plan.field_sizes()), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        if prec == "mixed":
+            rc, o, it = plan.solve_mixed(br_d, TOL, phi)
+        else:
+            rc, it = plan.solve(br_d, TOL, phi)
+        st = plan.stats()
+        plan.field(phi, br_d, B)
+        return it, st
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters, ka, kb, na, nb, launches = 0, 0.0, 0.0, 0.0, 0.0, 0
+    for _ in range(steps):
+        it, st = step()
+        iters += it
+        ka += st["kernel_ms"][0]
+        kb += st["kernel_ms"][1]
+        na += st["kernel_ms"][2]
+        nb += st["kernel_ms"][3]
+        launches += st["launches"] + 2  # + the field's two kernels
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ms_max = reduce_max(ms, dist, dev)
+    iters_all = reduce_sum(iters, dist, dev)
+    value = iters_all / (ms_max * 1e-3)
+    es = 4 if prec == "mixed" else 8
+    n = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    bytes_per_iter = 9.0 * es * n  # 6 vectors touched by the matvec + 3 by the update
+    peaks, src = measured_peaks()
+    mv_ms = ka / max(na, 1)
+    up_ms = kb / max(nb, 1)
+    if prec == "fp64":
+        achieved = 2 * FP64_FMA_PER_POINT_MATVEC * n / (mv_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_matvec<PF64>", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None,
+                "peak_source": "FP64 FMA units x max SM clock: 152 x 2/clk x 2 flop x 2.07 GHz",
+                "hbm_GB_s": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9,
+                "hbm_frac_of_measured": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    else:
+        achieved = info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_matvec<%s>" % ("PDF" if prec == "df" else "PF32"),
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % src}
+    roof["avg_launch_ms"] = mv_ms
+    roof["algorithmic_bytes_per_launch"] = info["bytes_matvec"]
+    roof["update_kernel"] = {"avg_launch_ms": up_ms,
+                             "GB_s": info["bytes_update"] / (up_ms * 1e-3) / 1e9 if up_ms else None,
+                             "frac_of_measured_hbm": (info["bytes_update"] / (up_ms * 1e-3) / 1e9
+                                                      / peaks["hbm_gbs"]) if up_ms else None}
+    out = {"value": value, "unit": "iters/s", "ms_per_step": ms_max / steps, "dtype": DTYPES[prec],
+           "iters_per_solve": iters / steps, "hbm_gbs": value / ws * bytes_per_iter / 1e9,
+           "bytes_per_iter": bytes_per_iter, "roofline": roof, "gpu_launches": launches,
+           "clocks": clk, "steps": steps, "warmup": warmup}
+    if with_e2e:
+        # end to end through the same C ABI with pinned host buffers
+        br_h = torch.from_numpy(br).pin_memory().numpy()
+        phi_h = torch.zeros(SHAPE, dtype=torch.float64).pin_memory().numpy()
+        B_h = torch.zeros(B.numel(), dtype=torch.float64).pin_memory().numpy()
+        e2e_steps = max(1, min(steps, 2))
+        barrier(dist, dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(e2e_steps):
+            if prec == "mixed":
+                rc, o, it = plan.solve_mixed(br_h, TOL, phi_h)
+            else:
+                rc, it = plan.solve(br_h, TOL, phi_h)
+            plan.field(phi_h, br_h, B_h)
+            e_iters += it
+        torch.cuda.synchronize(dev)
+        e_dt = reduce_max(time.perf_counter() - t0, dist, dev)
+        e_iters = reduce_sum(e_iters, dist, dev)
+        out["e2e"] = {"value": e_iters / e_dt, "unit": "iters/s",
+                      "h2d_bytes_per_step": br_h.nbytes * 2 + phi_h.nbytes,  # solve Br; field Br, Phi
+                      "d2h_bytes_per_step": phi_h.nbytes + B_h.nbytes}
+    plan.close()
+    return out
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1709_01126_gb300 import pot3d
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    pot3d.load()
+    br = make_br()
+    br_d = torch.from_numpy(br).to(dev)
+    head = measure(pot3d, torch, dev, dist, br, br_d, args.prec, args.steps, args.warmup)
+    result = {
+        "metric": METRIC, "value": head["value"], "unit": "iters/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
+        "data": "synthetic",
+        "config": {"workload": "potential-field PCG 151x301x601, r geometric 1.02, "
+                               "dipole + 200 bipoles (seed 1709), tol 1e-10, + field",
+                   "grid": list(SHAPE), "tol": TOL, "precision": args.prec,
+                   "iters_per_solve": head["iters_per_solve"],
+                   "l2": "inputs larger than L2 (each vector %.0f MB)"
+                         % ((4 if args.prec == "mixed" else 8) * SHAPE[0] * SHAPE[1] * SHAPE[2] / 1e6),
+                   "parallelism": "replicas x%d" % ws},
+        "hbm_gbs": head["hbm_gbs"], "bytes_per_iter": head["bytes_per_iter"],
+        "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+    }
+    variants = {}
+    for pv in args.variants:
+        if pv == args.prec:
+            continue
+        v = measure(pot3d, torch, dev, dist, br, br_d, pv, steps=2, warmup=1, with_e2e=False)
+        variants[pv] = v
+    if variants:
+        result["variants"] = variants
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(br)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    barrier(dist, dev)
+    return 0
+
+
+def run_profile_case(args):
+    """Short solve for ncu: the same 151x301x601 problem, capped at a few
+    PCG iterations so a capture ends quickly."""
+    import torch
+
+    from paper_1709_01126_gb300 import pot3d
+
+    pot3d.load()
+    br_d = torch.from_numpy(make_br()).cuda()
+    plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=args.profile_case,
+                      max_iters=args.profile_iters, use_graphs=-1)
+    phi = torch.zeros(SHAPE, dtype=torch.float64, device="cuda")
+    if args.profile_case == "mixed":
+        plan.set_opts(max_iters=args.profile_iters, use_graphs=-1, max_outer=1)
+        plan.solve_mixed(br_d, TOL, phi, check=False)
+    else:
+        plan.solve(br_d, TOL, phi, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "iters": plan.stats()["iters"]}))
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "df", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="df,mixed",
+                    help="other precisions measured briefly on the same line ('' for none)")
+    ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
+                    help="run a short capped solve for ncu and exit")
+    ap.add_argument("--profile-iters", type=int, default=6)
+    args = ap.parse_args()
+    args.variants = [v for v in args.variants.split(",") if v]
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

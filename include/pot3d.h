@@ -23,7 +23,8 @@
  * (cudaMalloc / torch CUDA tensors; no copy) or host pointers (staged
  * through device memory inside the call; pinned host memory makes those
  * copies asynchronous).  All GPU work runs on the plan's stream (set with
- * pot3d_set_stream; default: the legacy default stream).  A call that
+ * pot3d_set_stream; default: a blocking stream the plan creates, ordered
+ * with the legacy default stream).  A call that
  * returns a result on the host (iteration counts, residuals) synchronises
  * that stream before returning.
  *
@@ -90,7 +91,7 @@ typedef struct {
 
 /* Solver options; zero-initialised fields take the defaults. */
 typedef struct {
-  int max_iters;      /* PCG iteration cap (inner cap for MIXED); 0: 4*(nr+nt+np)*8 */
+  int max_iters;      /* PCG iteration cap (inner cap for MIXED); 0: 100*(nr+nt+np) */
   int use_x0;         /* 1: phi holds the initial guess on entry of pot3d_solve      */
   int chunk;          /* iterations enqueued between host polls; 0: automatic        */
   int use_graphs;     /* 0: automatic (graphs on), 1: on, -1: off                    */
@@ -108,6 +109,7 @@ typedef struct {
                           or the recomputed FP64 residual (MIXED)                */
   double kernel_ms[4]; /* with time_kernels: summed event time of the matvec     */
                        /* kernel, the update kernel, and their launch counts     */
+  long long launches;  /* kernels the last solve or field call launched          */
 } pot3d_stats_t;
 
 /* Static facts about a plan (for measurement and sizing). */

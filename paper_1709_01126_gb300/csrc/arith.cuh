@@ -51,6 +51,18 @@ __device__ __forceinline__ dfl df_add(dfl x, dfl y) {
   return z;
 }
 
+// SloppyDWPlusDW: the relative error bound holds when x and y have the same
+// sign; under cancellation the absolute error stays within about 2^-46 of
+// |x| + |y|, which is the accuracy an accumulator (x~, r, p~) needs.
+__device__ __forceinline__ dfl df_add_sloppy(dfl x, dfl y) {
+  float sh, sl;
+  two_sum(x.h, y.h, sh, sl);
+  sl = __fadd_rn(sl, __fadd_rn(x.l, y.l));
+  dfl z;
+  fast_two_sum(sh, sl, z.h, z.l);
+  return z;
+}
+
 __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
   float ch = __fmul_rn(x.h, y.h);
   float cl1 = __fmaf_rn(x.h, y.h, -ch);
@@ -159,7 +171,9 @@ struct PDF {
   static __device__ __forceinline__ void stv(st *p, val v) { *p = make_float2(v.h, v.l); }
   static __device__ __forceinline__ val zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ scal scal_from(double x) { return df_from_double(x); }
-  static __device__ __forceinline__ val fma(scal a, val x, val y) { return df_add(y, df_mul(a, x)); }
+  static __device__ __forceinline__ val fma(scal a, val x, val y) {
+    return df_add_sloppy(y, df_mul(a, x));
+  }
   static __device__ __forceinline__ sacc s_init(val c) { return {c.h, c.l}; }
   static __device__ __forceinline__ void s_add(sacc &s, coef c, val x) {
     cacc_add_prod(s, dfl{c.x, c.y}, x);

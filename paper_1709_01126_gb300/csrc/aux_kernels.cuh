@@ -202,7 +202,7 @@ __global__ void k_finish(const ProbDev *probs, const double *__restrict__ c64, d
 template <int NT>
 __global__ void __launch_bounds__(NT)
     k_inner_rhs(const double *__restrict__ r64, const float *__restrict__ dinv32, int nr, int nt,
-                int np, int pitch, double scale, float *r32, double *part) {
+                int ntp, int np, int pitch, double scale, float *r32, double *part) {
   __shared__ double red[NT / 32];
   const size_t R = (size_t)nr * nt, n = R * np;
   double s2 = 0.0, sw = 0.0;
@@ -213,8 +213,9 @@ __global__ void __launch_bounds__(NT)
     const float f = __double2float_rn(scale * r64[o]);
     r32[o] = f;
     const double d = (double)f;
+    const size_t i = row / nt, j = row - i * nt;
     s2 = fma(d, d, s2);
-    sw = fma((double)dinv32[row] * d, d, sw);
+    sw = fma((double)dinv32[i * ntp + j] * d, d, sw);
   }
   const double t2 = block_sum<NT>(s2, red);
   const double tw = block_sum<NT>(sw, red);

@@ -21,11 +21,13 @@
 // Every reduction is deterministic: each work item writes its partial to a
 // fixed slot, and the last block sums the slots in a fixed order.
 #pragma once
+#include <cuda.h>
+
 #include "arith.cuh"
 
 namespace pot3d {
 
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3, ST_TIMEOUT = 4 };
 
 // FP64 metric table of the unscaled operator, [7][nr*nt]:
 //   0: D (diagonal, includes the 2 c^r term of the source-surface ghost)
@@ -52,9 +54,19 @@ struct SolveState {
   int pad_;
 };
 
+// TMA descriptors of one problem's iteration vectors (device memory).
+// r, p0, p1: boxes of (TK + 2 AL) x (TJ + 2) x 1; x: TK x TJ x 1; *w: the
+// AL-wide periodic wrap columns; cf: the six metric coefficients of TJ
+// theta rows of one r plane (box TJ x 1 x 6 over the table [6][nr][ntp]).
+struct TmaSet {
+  CUtensorMap r, p0, p1, x, rw, p0w, p1w, cf;
+};
+
 // One problem (one solve) as the kernels see it.
 struct ProbDev {
   int nr, nt, np, pitch;
+  int ntp;            // row pitch of the metric tables (nt rounded up to 4)
+  int pad0_;
   int nJ, nK, ic, nI; // matvec tiles along theta, phi; i-chunk length; i-chunks
   int tiles_a;        // nJ*nK*nI
   int rows_b;         // rows per update work item
@@ -62,10 +74,11 @@ struct ProbDev {
   int pad_;
   long long plane; // nt*pitch
   void *x, *r, *p0, *p1, *q;
-  const void *coef;  // scaled metric table [6][nr*nt]: Dinv, n_r+, n_r-, n_t+, n_t-, n_ph
+  const void *coef;  // scaled metric table [6][nr][ntp]: Dinv, n_r+, n_r-, n_t+, n_t-, n_ph
   double *part_a;    // [tiles_a]
   double *part_b;    // [2*tiles_b]
   SolveState *st;
+  const TmaSet *tma;
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -99,23 +112,113 @@ __device__ __forceinline__ double block_sum_array(const double *a, int n, int st
   return block_sum<NT>(s, red);
 }
 
+// ------------------------------------------------------------ TMA / mbarrier
+// Inline PTX for the Blackwell bulk-tensor copy engine: one elected thread
+// issues cp.async.bulk.tensor box loads into shared memory; completion is
+// tracked by transaction-counting mbarriers.  Every wait is bounded by the
+// global timer so a lost transfer ends as a TIMEOUT status, not a hang.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok)
+               : "r"(smem_u32(bar)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull; // 2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory plan of the matvec tile, shared by host (sizing) and device.
+template <int ES, int TJ, int VK, int S>
+struct MvLayout {
+  static constexpr int AL = 16 / ES;        // elements per 16 bytes (TMA x alignment)
+  static constexpr int TK = 32 * VK;        // phi columns per tile
+  static constexpr int RH = TJ + 2, RW = TK + 2;
+  static constexpr int BW = TK + 2 * AL;    // main box width: k0-AL .. k0+TK+AL-1
+  static constexpr int a128(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int SZ_RP = a128(RH * BW * ES);
+  static constexpr int SZ_X = a128(TJ * TK * ES);
+  static constexpr int SZ_W = a128(RH * AL * ES);
+  static constexpr int OFF_R = 0, OFF_P = SZ_RP, OFF_X = 2 * SZ_RP;
+  static constexpr int OFF_RWL = OFF_X + SZ_X, OFF_PWL = OFF_RWL + SZ_W;
+  static constexpr int OFF_RWR = OFF_PWL + SZ_W, OFF_PWR = OFF_RWR + SZ_W;
+  static constexpr int SZ_C = a128(6 * TJ * ES);
+  static constexpr int OFF_C = OFF_PWR + SZ_W;
+  static constexpr int STAGE = OFF_C + SZ_C;
+  static constexpr int RING = a128(3 * RH * RW * ES);
+  static constexpr int BYTES = S * STAGE + RING + 8 * S;
+};
+
 // ------------------------------------------------------------ k_matvec
 // Work item = (problem, tile).  A tile is TJ theta rows x TK = 32*VK phi
 // columns, marching over an i-chunk [i0, i1).  Each warp owns one theta row;
-// lane l owns phi columns k0 + l + 32 v.  Per plane the block stages p~_new
-// on the (TJ+2) x (TK+2) halo region in shared memory (three rotating plane
-// buffers, one barrier per plane); the r-neighbours come from registers.
-template <class A, int TJ, int VK>
-__global__ void __launch_bounds__(32 * TJ)
+// lane l owns phi columns k0 + l + 32 v.
+// Data movement: for every r-plane of the chunk (plus one halo plane on each
+// side) thread 0 issues TMA box loads of r and p~_old over the (TJ+2) x
+// (TK+2) halo region (x from k0-AL so the box start is 16-byte aligned;
+// theta rows outside the grid arrive zero-filled), of x~ over the owned
+// cells, and of the two periodic wrap columns when the tile touches phi = 0
+// or 2 pi.  S stages run ahead of the compute.  Per plane the block forms
+// p~_new = r + beta p~_old on the region into a 3-plane ring (one barrier per
+// plane), stores p~_new and the deferred x~ += alpha_prev p~_old for its own
+// cells, and applies the stencil to the previous plane (r-neighbours from
+// registers).  The sigma partial closes with the last-block reduction.
+template <class A, int TJ, int VK, int S>
+__global__ void __launch_bounds__(32 * TJ, 3)
     k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work, int nwork) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
-  constexpr int TK = 32 * VK, RW = TK + 2, RH = TJ + 2, RC = RW * RH, NT = 32 * TJ;
-  __shared__ val sm[3][RH][RW];
+  using LY = MvLayout<(int)sizeof(st), TJ, VK, S>;
+  constexpr int AL = LY::AL, TK = LY::TK, RH = LY::RH, RW = LY::RW, BW = LY::BW, NT = 32 * TJ;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  val(*ring)[RH][RW] = reinterpret_cast<val(*)[RH][RW]>(smraw + S * LY::STAGE);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + S * LY::STAGE + LY::RING);
   __shared__ double red[NT / 32];
   __shared__ int s_last;
   const int lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32 + lane;
+  if (tid == 0) {
+    for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t seq = 0; // planes consumed by this block so far (stage/parity counter)
 
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
@@ -124,108 +227,201 @@ __global__ void __launch_bounds__(32 * TJ)
     if (ldcg(&stt->status) != ST_RUNNING) continue;
     const int kit = ldcg(&stt->iter) + 1; // this iteration
     const int t = wi.y;
-    const int nr = P.nr, nt = P.nt, np = P.np, pitch = P.pitch;
+    const int nr = P.nr, nt = P.nt, np = P.np, pitch = P.pitch, ntp = P.ntp;
+    const long long plane = P.plane;
     const int tk = t % P.nK, tj = (t / P.nK) % P.nJ, ci = t / (P.nK * P.nJ);
     const int j0 = tj * TJ, k0 = tk * TK, i0 = ci * P.ic;
     const int i1 = min(nr, i0 + P.ic);
-    const st *__restrict__ r = static_cast<const st *>(P.r);
-    const st *__restrict__ pold = static_cast<const st *>((kit & 1) ? P.p0 : P.p1);
+    const bool first = (kit == 1);
+    const TmaSet *T = P.tma;
+    const CUtensorMap *m_r = &T->r, *m_x = &T->x;
+    const CUtensorMap *m_po = (kit & 1) ? &T->p0 : &T->p1;
+    const CUtensorMap *m_rw = &T->rw, *m_pow = (kit & 1) ? &T->p0w : &T->p1w, *m_cf = &T->cf;
     st *__restrict__ pnew = static_cast<st *>((kit & 1) ? P.p1 : P.p0);
     st *__restrict__ x = static_cast<st *>(P.x);
     st *__restrict__ q = static_cast<st *>(P.q);
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
-    const size_t R = (size_t)nr * nt;
+    const size_t R = (size_t)nr * ntp; // table slab of one coefficient
     const typename A::scal beta = A::scal_from(kit > 1 ? ldcg(&stt->beta[(kit - 1) & 1]) : 0.0);
     const typename A::scal alpha_prev =
         A::scal_from(kit > 1 ? ldcg(&stt->alpha[(kit - 1) & 1]) : 0.0);
-    const bool first = (kit == 1);
+    const bool wl = (k0 == 0), wr = (k0 + TK >= np);
+    const int xl = ((np - 1) / AL) * AL, ol = (np - 1) - xl;
+    const int ps = max(i0 - 1, 0), pe = min(i1, nr - 1), L = pe - ps + 1;
 
-    // Stage plane ip into buffer b: p~_new = r + beta p~_old on the halo
-    // region; the owning tile also stores p~_new and updates x~.
-    auto load_plane = [&](int ip, int b, bool own) {
-      const size_t pbase = (size_t)ip * P.plane;
-      for (int c = tid; c < RC; c += NT) {
-        const int rr = c / RW, cc = c - rr * RW;
-        const int jj = j0 - 1 + rr, kk = k0 - 1 + cc;
-        val v = A::zero();
-        if (jj >= 0 && jj < nt && kk <= np) {
-          const int km = kk < 0 ? kk + np : (kk >= np ? kk - np : kk);
-          const size_t off = pbase + (size_t)jj * pitch + km;
-          const val rv = A::ld(r + off);
-          if (first) {
-            v = rv;
-          } else {
-            const val po = A::ld(pold + off);
-            v = A::fma(beta, po, rv);
-            if (own && rr >= 1 && rr <= TJ && cc >= 1 && cc <= TK && kk < np) {
-              const val xv = A::ld(x + off);
-              A::stv(x + off, A::fma(alpha_prev, po, xv));
-            }
-          }
-          if (own && rr >= 1 && rr <= TJ && cc >= 1 && cc <= TK && kk < np) A::stv(pnew + off, v);
-        }
-        sm[b][rr][cc] = v;
+    auto issue = [&](int tt) {
+      const int ip = ps + tt;
+      const uint32_t sidx = (seq + tt) % S;
+      unsigned char *base = smraw + sidx * LY::STAGE;
+      uint64_t *bar = &bars[sidx];
+      const bool own = (ip >= i0 && ip < i1);
+      const uint32_t box = RH * BW * sizeof(st), wbox = RH * AL * sizeof(st);
+      uint32_t bytes = box + 6u * TJ * (uint32_t)sizeof(st);
+      if (!first) bytes += box + (own ? TJ * TK * (uint32_t)sizeof(st) : 0u);
+      const uint32_t nw = (wl ? 1u : 0u) + (wr ? 1u : 0u);
+      bytes += nw * wbox * (first ? 1u : 2u);
+      mbar_expect_tx(bar, bytes);
+      // coefficients of plane ip-1: its stencil is applied once plane ip is in
+      tma_load_3d(base + LY::OFF_C, m_cf, bar, j0, ip - 1, 0);
+      tma_load_3d(base + LY::OFF_R, m_r, bar, k0 - AL, j0 - 1, ip);
+      if (!first) {
+        tma_load_3d(base + LY::OFF_P, m_po, bar, k0 - AL, j0 - 1, ip);
+        if (own) tma_load_3d(base + LY::OFF_X, m_x, bar, k0, j0, ip);
+      }
+      if (wl) {
+        tma_load_3d(base + LY::OFF_RWL, m_rw, bar, xl, j0 - 1, ip);
+        if (!first) tma_load_3d(base + LY::OFF_PWL, m_pow, bar, xl, j0 - 1, ip);
+      }
+      if (wr) {
+        tma_load_3d(base + LY::OFF_RWR, m_rw, bar, 0, j0 - 1, ip);
+        if (!first) tma_load_3d(base + LY::OFF_PWR, m_pow, bar, 0, j0 - 1, ip);
       }
     };
+    if (tid == 0) {
+      for (int tt = 0; tt < min(S, L); tt++) issue(tt);
+    }
 
     const int j = j0 + wy;
     const bool jv = j < nt;
     typename A::dacc tacc = A::d_init();
-    val prv[VK], cur[VK];
-    int bp = 0, bc = 1, bn = 2;
-    if (i0 > 0) load_plane(i0 - 1, bp, false);
-    load_plane(i0, bc, true);
-    __syncthreads();
+    val prv[VK], cur[VK], nxt[VK];
 #pragma unroll
-    for (int v = 0; v < VK; v++) {
-      prv[v] = (i0 > 0) ? sm[bp][wy + 1][lane + 32 * v + 1] : A::zero();
-      cur[v] = sm[bc][wy + 1][lane + 32 * v + 1];
-    }
-    for (int i = i0; i < i1; i++) {
-      // metric coefficients of row (i, j); uniform across the warp
-      coef cDi{}, cRp{}, cRm{}, cTp{}, cTm{}, cPh{};
-      if (jv) {
-        const size_t row = (size_t)i * nt + j;
-        cDi = cf[row];
-        cRp = cf[R + row];
-        cRm = cf[2 * R + row];
-        cTp = cf[3 * R + row];
-        cTm = cf[4 * R + row];
-        cPh = cf[5 * R + row];
+    for (int v = 0; v < VK; v++) prv[v] = cur[v] = A::zero();
+    bool bad = false;
+
+    // metric coefficients of row (i, j) for the stencil of the current step
+    coef cc_[6];
+    // stencil of plane i from the ring (in-plane neighbours) and registers
+    auto stencil = [&](int i, const coef (&c)[6]) {
+      const int sl = i % 3;
+      typename A::dacc racc = A::d_init();
+      const size_t rowoff = (size_t)i * plane + (size_t)j * pitch;
+#pragma unroll
+      for (int v = 0; v < VK; v++) {
+        const int cc = lane + 32 * v + 1;
+        typename A::sacc s = A::s_init(cur[v]);
+        A::s_add(s, c[1], nxt[v]);
+        A::s_add(s, c[2], prv[v]);
+        A::s_add(s, c[3], ring[sl][wy + 2][cc]);
+        A::s_add(s, c[4], ring[sl][wy][cc]);
+        A::s_add(s, c[5], ring[sl][wy + 1][cc - 1]);
+        A::s_add(s, c[5], ring[sl][wy + 1][cc + 1]);
+        const val qv = A::s_get(s);
+        const int kk = k0 + cc - 1;
+        if (kk < np) {
+          A::stv(q + rowoff + kk, qv);
+          A::d_add(racc, cur[v], qv);
+        }
       }
-      const bool has_next = (i + 1 < nr);
-      if (has_next) load_plane(i + 1, bn, i + 1 < i1);
-      __syncthreads();
-      if (jv) {
-        typename A::dacc racc = A::d_init();
-        const size_t rowoff = (size_t)i * P.plane + (size_t)j * pitch;
+      A::d_addw(tacc, c[0], racc);
+    };
+
+    int tt = 0;
+    for (; tt < L; tt++) {
+      const int ip = ps + tt;
+      const uint32_t sidx = (seq + tt) % S;
+      const uint32_t parity = ((seq + tt) / S) & 1u;
+      const unsigned char *base = smraw + sidx * LY::STAGE;
+      const st(*rs)[BW] = reinterpret_cast<const st(*)[BW]>(base + LY::OFF_R);
+      const st(*pso)[BW] = reinterpret_cast<const st(*)[BW]>(base + LY::OFF_P);
+      const st(*xs)[TK] = reinterpret_cast<const st(*)[TK]>(base + LY::OFF_X);
+      const st(*rwl)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_RWL);
+      const st(*pwl)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_PWL);
+      const st(*rwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_RWR);
+      const st(*pwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_PWR);
+      const coef(*cs)[TJ] = reinterpret_cast<const coef(*)[TJ]>(base + LY::OFF_C);
+      const int sl = ip % 3;
+      bad = !mbar_wait(&bars[sidx], parity);
+#pragma unroll
+      for (int m = 0; m < 6; m++) cc_[m] = cs[m][wy];
+      const bool own = (ip >= i0 && ip < i1);
+      // owned cells: natural (warp = theta row, lane = phi) mapping
+      {
+        const int rr = wy + 1;
+        const size_t off = (size_t)ip * plane + (size_t)j * pitch;
 #pragma unroll
         for (int v = 0; v < VK; v++) {
-          const int cc = lane + 32 * v + 1;
-          const val nxt = has_next ? sm[bn][wy + 1][cc] : A::zero();
-          typename A::sacc s = A::s_init(cur[v]);
-          A::s_add(s, cRp, nxt);
-          A::s_add(s, cRm, prv[v]);
-          A::s_add(s, cTp, sm[bc][wy + 2][cc]);
-          A::s_add(s, cTm, sm[bc][wy][cc]);
-          A::s_add(s, cPh, sm[bc][wy + 1][cc - 1]);
-          A::s_add(s, cPh, sm[bc][wy + 1][cc + 1]);
-          const val qv = A::s_get(s);
-          const int kk = k0 + cc - 1;
+          const int cc = lane + 32 * v + 1, kk = k0 + cc - 1;
+          val pn = A::zero();
           if (kk < np) {
-            A::stv(q + rowoff + kk, qv);
-            A::d_add(racc, cur[v], qv);
+            const val rv = A::ld(&rs[rr][cc - 1 + AL]);
+            if (first) {
+              pn = rv;
+            } else {
+              const val po = A::ld(&pso[rr][cc - 1 + AL]);
+              pn = A::fma(beta, po, rv);
+              if (own && jv) {
+                const val xv = A::ld(&xs[wy][cc - 1]);
+                A::stv(x + off + kk, A::fma(alpha_prev, po, xv));
+              }
+            }
+            if (own && jv) A::stv(pnew + off + kk, pn);
+          } else if (kk == np) {
+            const val rv = A::ld(&rwr[rr][0]);
+            pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
           }
-          prv[v] = cur[v];
-          cur[v] = nxt;
+          ring[sl][rr][cc] = pn;
         }
-        A::d_addw(tacc, cDi, racc);
       }
-      const int tmp = bp;
-      bp = bc;
-      bc = bn;
-      bn = tmp;
+      // halo cells: rows 0 and RH-1 (all columns), columns 0 and RW-1
+      for (int h = tid; h < 2 * RW + 2 * TJ; h += NT) {
+        int rr, cc;
+        if (h < 2 * RW) {
+          rr = (h < RW) ? 0 : RH - 1;
+          cc = (h < RW) ? h : h - RW;
+        } else {
+          const int g = h - 2 * RW;
+          rr = 1 + (g >> 1);
+          cc = (g & 1) ? RW - 1 : 0;
+        }
+        const int kk = k0 - 1 + cc;
+        val pn = A::zero();
+        if (kk < 0) {
+          const val rv = A::ld(&rwl[rr][ol]);
+          pn = first ? rv : A::fma(beta, A::ld(&pwl[rr][ol]), rv);
+        } else if (kk < np) {
+          const val rv = A::ld(&rs[rr][cc - 1 + AL]);
+          pn = first ? rv : A::fma(beta, A::ld(&pso[rr][cc - 1 + AL]), rv);
+        } else if (kk == np) {
+          const val rv = A::ld(&rwr[rr][0]);
+          pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
+        }
+        ring[sl][rr][cc] = pn;
+      }
+      if (__syncthreads_or(bad)) {
+        bad = true;
+        break;
+      }
+      if (tid == 0 && tt + S < L) issue(tt + S);
+#pragma unroll
+      for (int v = 0; v < VK; v++) nxt[v] = ring[sl][wy + 1][lane + 32 * v + 1];
+      if (ip - 1 >= i0 && jv) stencil(ip - 1, cc_);
+#pragma unroll
+      for (int v = 0; v < VK; v++) {
+        prv[v] = cur[v];
+        cur[v] = nxt[v];
+      }
     }
+    if (bad) {
+      // drain this tile's transfers still in flight (bounded), then report
+      if (tid == 0) {
+        for (int u = tt; u < min(L, tt + S); u++)
+          mbar_wait(&bars[(seq + u) % S], ((seq + u) / S) & 1u);
+        stt->status = ST_TIMEOUT;
+      }
+      __syncthreads();
+      seq += L;
+      break;
+    }
+    if (i1 == nr && jv) {
+#pragma unroll
+      for (int v = 0; v < VK; v++) nxt[v] = A::zero();
+      const size_t row = (size_t)(nr - 1) * ntp + j;
+#pragma unroll
+      for (int m = 0; m < 6; m++) cc_[m] = cf[m * R + row];
+      stencil(nr - 1, cc_);
+    }
+    seq += L;
 
     const double mine = jv ? A::d_get(tacc) : 0.0;
     const double tot = block_sum<NT>(mine, red);
@@ -259,7 +455,7 @@ __global__ void __launch_bounds__(32 * TJ)
 // take 16-byte vectors along phi.  r -= alpha q; per row s = sum r^2, then
 // ||r||^2 += s and rho += D^-1 s.  The last block closes the iteration.
 template <class A, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 3)
     k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work, int nwork) {
   using val = typename A::val;
   using st = typename A::st;
@@ -285,19 +481,33 @@ __global__ void __launch_bounds__(NT)
     typename A::dacc arr = A::d_init(), arho = A::d_init();
     for (int row = row0 + wy; row < row1; row += NW) {
       const int i = row / nt, j = row - i * nt;
-      const coef dinv = cf[row];
+      const coef dinv = cf[(size_t)i * P.ntp + j];
       const size_t base = (size_t)i * P.plane + (size_t)j * pitch;
       typename A::dacc s = A::d_init();
-      for (int k = lane * V; k < np; k += 32 * V) {
-        val rv[V], qv[V];
-        A::ldv(r + base + k, rv);
-        A::ldv(q + base + k, qv);
+      // U 16-byte vectors of r and of q per lane in flight per step
+      constexpr int U = 4;
+      for (int k = lane * V; k < np; k += 32 * V * U) {
+        val rv[U][V], qv[U][V];
 #pragma unroll
-        for (int u = 0; u < V; u++) {
-          rv[u] = A::fma(nalpha, qv[u], rv[u]);
-          if (k + u < np) A::d_add(s, rv[u], rv[u]);
+        for (int u = 0; u < U; u++) {
+          const int ku = k + 32 * V * u;
+          if (ku < np) {
+            A::ldv(r + base + ku, rv[u]);
+            A::ldv(q + base + ku, qv[u]);
+          }
         }
-        A::stvv(r + base + k, rv);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int ku = k + 32 * V * u;
+          if (ku < np) {
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+              rv[u][e] = A::fma(nalpha, qv[u][e], rv[u][e]);
+              if (ku + e < np) A::d_add(s, rv[u][e], rv[u][e]);
+            }
+            A::stvv(r + base + ku, rv[u]);
+          }
+        }
       }
       // ||r||^2 += s ; rho += Dinv * s
       A::d_merge(arr, s);

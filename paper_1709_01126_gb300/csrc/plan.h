@@ -14,6 +14,8 @@ enum { AR_F64 = 0, AR_DF = 1, AR_F32 = 2 };
 // Matvec tile shape: TJ theta rows (one warp each) x 32*VK phi columns.
 constexpr int kTJ = 8;
 constexpr int kVK = 2;
+constexpr int kStages8 = 3; // TMA stages for 8-byte elements (FP64, double-float)
+constexpr int kStages4 = 4; // TMA stages for FP32
 constexpr int kUpdThreads = 256;
 constexpr int kAuxThreads = 256;
 
@@ -27,11 +29,14 @@ struct ArithData {
   int graph_chunk = 0;
   cudaStream_t graph_stream = nullptr;
   ProbDev h_prob{};
+  TmaSet *d_tma = nullptr;
+  TmaSet h_tma{};
   bool ready = false;
 };
 
 struct Plan {
   int nr = 0, nt = 0, np = 0, pitch = 0, prec = 0;
+  int ntp = 0; // metric-table row pitch (nt rounded up to 4)
   size_t R = 0, n = 0, npad = 0;
   // host mesh (Sec. 2.2) and tables
   std::vector<double> rf, tf, rc, tc, drc, dtc;

@@ -176,25 +176,34 @@ static int upload(T **dst, const std::vector<T> &h) {
   return POT3D_OK;
 }
 
-// Device copy of the iteration table in the arithmetic's coefficient type.
+// Device copy of the iteration table in the arithmetic's coefficient type,
+// laid out [6][nr][ntp] (theta rows padded to a multiple of 4 so that every
+// row of the table starts on a 16-byte boundary for the TMA).
 int ensure_arith(Plan *P, int ai) {
   ArithData &A = P->ar[ai];
   if (A.ready) return POT3D_OK;
   std::vector<double> t;
   scaled_table(P, t);
+  const int ntp = P->ntp;
+  const size_t RP = (size_t)P->nr * ntp;
+  std::vector<double> tp(6 * RP, 0.0);
+  for (int m = 0; m < 6; m++)
+    for (int i = 0; i < P->nr; i++)
+      for (int j = 0; j < P->nt; j++)
+        tp[m * RP + (size_t)i * ntp + j] = t[m * P->R + (size_t)i * P->nt + j];
   int rc = POT3D_OK;
   if (ai == AR_F64) {
-    rc = upload((double **)&A.coef, t);
+    rc = upload((double **)&A.coef, tp);
   } else if (ai == AR_DF) {
-    std::vector<float2> h(t.size());
-    for (size_t u = 0; u < t.size(); u++) {
-      const float hi = (float)t[u];
-      h[u] = make_float2(hi, (float)(t[u] - (double)hi));
+    std::vector<float2> h(tp.size());
+    for (size_t u = 0; u < tp.size(); u++) {
+      const float hi = (float)tp[u];
+      h[u] = make_float2(hi, (float)(tp[u] - (double)hi));
     }
     rc = upload((float2 **)&A.coef, h);
   } else {
-    std::vector<float> h(t.size());
-    for (size_t u = 0; u < t.size(); u++) h[u] = (float)t[u];
+    std::vector<float> h(tp.size());
+    for (size_t u = 0; u < tp.size(); u++) h[u] = (float)tp[u];
     rc = upload((float **)&A.coef, h);
   }
   if (rc) return rc;
@@ -306,6 +315,7 @@ pot3d_plan_t *pot3d_plan(const pot3d_grid_t *g, const pot3d_bc_t *bc) {
   P->R = (size_t)g->nr * g->nt;
   P->n = P->R * g->np;
   P->pitch = (g->np + 31) / 32 * 32;
+  P->ntp = (g->nt + 3) / 4 * 4;
   P->npad = P->R * P->pitch;
   int rc = build_mesh(P, g);
   if (rc) {

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cudaTypedefs.h>
+
 #include "aux_kernels.cuh"
 #include "plan.h"
 
@@ -81,6 +83,7 @@ void plan_free(Plan *P) {
     cudaFree(A.d_state);
     cudaFree(A.part_a);
     cudaFree(A.part_b);
+    cudaFree(A.d_tma);
   }
   for (auto e : P->ev) cudaEventDestroy(e);
   cudaFree(P->d_work_a);
@@ -106,9 +109,102 @@ void plan_free(Plan *P) {
 
 // ------------------------------------------------------------- iteration
 template <class A>
+struct MvCfg {
+  static constexpr int S = sizeof(typename A::st) == 8 ? kStages8 : kStages4;
+  using LY = MvLayout<(int)sizeof(typename A::st), kTJ, kVK, S>;
+};
+
+template <class A>
+static int matvec_smem_setup() {
+  static int done = 0;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, kTJ, kVK, MvCfg<A>::S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         MvCfg<A>::LY::BYTES);
+    if (e != cudaSuccess) return cuda_status(e);
+    done = 1;
+  }
+  return POT3D_OK;
+}
+
+template <class A>
 static void launch_matvec(Plan *P, int ai) {
-  k_matvec<A, kTJ, kVK><<<P->tiles_a, dim3(32, kTJ), 0, P->stream>>>(P->ar[ai].d_prob, P->d_work_a,
-                                                                     P->tiles_a);
+  k_matvec<A, kTJ, kVK, MvCfg<A>::S><<<P->tiles_a, dim3(32, kTJ), MvCfg<A>::LY::BYTES, P->stream>>>(
+      P->ar[ai].d_prob, P->d_work_a, P->tiles_a);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D map over a padded vector [nr][nt][pitch] with a (bx, by, 1) box.
+static int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return POT3D_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)P->pitch, (cuuint64_t)P->nt, (cuuint64_t)P->nr};
+  cuuint64_t strides[2] = {(cuuint64_t)P->pitch * es, (cuuint64_t)P->nt * P->pitch * es};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = fn(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                  base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? POT3D_OK : POT3D_ERR_CUDA;
+}
+
+template <class A>
+static int build_tma(Plan *P, int ai) {
+  ArithData &D = P->ar[ai];
+  using LY = typename MvCfg<A>::LY;
+  constexpr int es = sizeof(typename A::st);
+  ProbDev &h = D.h_prob;
+  TmaSet &T = D.h_tma;
+  int rc = encode3d(&T.r, h.r, es, P, LY::BW, LY::RH);
+  if (!rc) rc = encode3d(&T.p0, h.p0, es, P, LY::BW, LY::RH);
+  if (!rc) rc = encode3d(&T.p1, h.p1, es, P, LY::BW, LY::RH);
+  if (!rc) rc = encode3d(&T.x, h.x, es, P, LY::TK, kTJ);
+  if (!rc) rc = encode3d(&T.rw, h.r, es, P, LY::AL, LY::RH);
+  if (!rc) rc = encode3d(&T.p0w, h.p0, es, P, LY::AL, LY::RH);
+  if (!rc) rc = encode3d(&T.p1w, h.p1, es, P, LY::AL, LY::RH);
+  if (!rc) {
+    // metric table [6][nr][ntp]: box of kTJ theta rows x 1 plane x 6 tables
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    cuuint64_t dims[3] = {(cuuint64_t)P->ntp, (cuuint64_t)P->nr, 6u};
+    cuuint64_t strides[2] = {(cuuint64_t)P->ntp * es, (cuuint64_t)P->nr * P->ntp * es};
+    cuuint32_t box[3] = {(cuuint32_t)kTJ, 1u, 6u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult cr = fn ? fn(&T.cf, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                          3, D.coef, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE)
+                     : CUDA_ERROR_NOT_FOUND;
+    if (cr != CUDA_SUCCESS) rc = POT3D_ERR_CUDA;
+  }
+  if (rc) return rc;
+  if (!D.d_tma) {
+    if (cudaMalloc(&D.d_tma, sizeof(TmaSet)) != cudaSuccess) {
+      cudaGetLastError();
+      return POT3D_ERR_OOM;
+    }
+  }
+  h.tma = D.d_tma;
+  if (cudaMemcpyAsync(D.d_tma, &T, sizeof(TmaSet), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
+    return POT3D_ERR_CUDA;
+  return matvec_smem_setup<A>();
 }
 template <class A>
 static void launch_update(Plan *P, int ai) {
@@ -172,6 +268,7 @@ static int iterate(Plan *P, int ai) {
       }
     }
     CTRY(cudaGetLastError());
+    P->stats.launches += 2LL * chunk;
     CTRY(cudaMemcpyAsync(P->h_state, D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                          P->stream));
     CTRY(cudaStreamSynchronize(P->stream));
@@ -207,6 +304,7 @@ static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, voi
   h.nt = P->nt;
   h.np = P->np;
   h.pitch = P->pitch;
+  h.ntp = P->ntp;
   h.nJ = P->nJ;
   h.nK = P->nK;
   h.ic = P->ic;
@@ -231,6 +329,7 @@ static int status_code(int st) {
   case ST_CONVERGED: return POT3D_OK;
   case ST_MAXIT: return POT3D_ERR_NOT_CONVERGED;
   case ST_BREAKDOWN: return POT3D_ERR_BREAKDOWN;
+  case ST_TIMEOUT: return POT3D_ERR_TIMEOUT;
   default: return POT3D_ERR_CUDA;
   }
 }
@@ -288,6 +387,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
        *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
   ArithData &D = P->ar[ai];
   fill_prob<A>(P, ai, x, r, p0, p1, q);
+  TRY(build_tma<A>(P, ai));
   cudaStream_t s = P->stream;
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
@@ -319,7 +419,9 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   }
   CTRY(cudaGetLastError());
   memset(&P->stats, 0, sizeof(P->stats));
+  P->stats.launches = x0 ? 7 : 4;
   TRY(iterate<A>(P, ai));
+  P->stats.launches += 1;
   k_finish<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, io.phi, 1);
   CTRY(cudaGetLastError());
   if (io.phi_host)
@@ -348,6 +450,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
        *q = ws_vec(P, 4, 4);
   double *x64 = ws_x64(P), *r64 = ws_r64(P);
   fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q);
+  TRY(build_tma<PF32>(P, AR_F32));
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
                        cudaMemcpyDeviceToDevice, s));
@@ -364,17 +467,19 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
                                                    P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
   const int gn = aux_grid(P, P->n);
-  const float *dinv32 = static_cast<const float *>(D.coef); // row 0 of the F32 table
+  const float *dinv32 = static_cast<const float *>(D.coef); // slab 0 of the F32 table
   const double inner_tol = P->opts.inner_tol > 0 ? P->opts.inner_tol : 1e-4;
   const int max_outer = P->opts.max_outer > 0 ? P->opts.max_outer : 30;
   const int inner_maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
   memset(&P->stats, 0, sizeof(P->stats));
+  P->stats.launches = 2 + (x0 ? 1 : 0);
   int n_outer = 0, n_inner = 0, status = POT3D_OK;
   double bb = 0.0, prev = INFINITY, relres = INFINITY;
   for (;;) {
     k_op64<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.br, P->d_S, P->d_c64, P->nr,
                                                    P->nt, P->np, 0, r64, P->pitch, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 2);
+    P->stats.launches += 2;
     CTRY(cudaGetLastError());
     CTRY(cudaMemcpyAsync(P->h_sums, P->d_sums, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     CTRY(cudaStreamSynchronize(s));
@@ -394,8 +499,8 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     // inner system L d = scale * r64 in FP32
     const double rms = std::sqrt(rr / (double)P->n);
     const double scale = std::ldexp(1.0, -std::ilogb(rms));
-    k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->np, P->pitch,
-                                                        scale, (float *)r, P->d_part);
+    k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->ntp, P->np,
+                                                        P->pitch, scale, (float *)r, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 4);
     CTRY(cudaMemsetAsync(x, 0, v4, s));
     CTRY(cudaMemsetAsync(p0, 0, v4, s));
@@ -403,6 +508,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     CTRY(cudaMemsetAsync(q, 0, v4, s));
     k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, (double)P->n, inner_tol, inner_maxit, 0,
                             1.0);
+    P->stats.launches += 4;
     CTRY(cudaGetLastError());
     TRY(iterate<PF32>(P, AR_F32));
     const SolveState &hs = *P->h_state;
@@ -412,9 +518,11 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
       break;
     }
     k_refine_update<<<gn, kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, x64, 1.0 / scale);
+    P->stats.launches += 1;
     n_outer++;
   }
   k_unpad<<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.phi, P->np, P->R, P->np);
+  P->stats.launches += 1;
   CTRY(cudaGetLastError());
   if (io.phi_host)
     CTRY(cudaMemcpyAsync(phi, io.phi, P->n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -469,6 +577,7 @@ int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double 
   const size_t tot = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
   k_field<<<aux_grid(P, tot), kAuxThreads, 0, s>>>(io.phi, d_br, P->d_poles, T, P->nr, P->nt, P->np,
                                                     io.B);
+  P->stats.launches = 2;
   CTRY(cudaGetLastError());
   if (io.B_host) CTRY(cudaMemcpyAsync(B, io.B, tot * sizeof(double), cudaMemcpyDeviceToHost, s));
   CTRY(cudaStreamSynchronize(s));

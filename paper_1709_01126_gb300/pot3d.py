@@ -54,7 +54,8 @@ class pot3d_opts_t(ctypes.Structure):
 
 class pot3d_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
-                ("relres", ctypes.c_double), ("kernel_ms", ctypes.c_double * 4)]
+                ("relres", ctypes.c_double), ("kernel_ms", ctypes.c_double * 4),
+                ("launches", ctypes.c_longlong)]
 
 
 class pot3d_info_t(ctypes.Structure):
@@ -213,7 +214,7 @@ class Plan:
         s = pot3d_stats_t()
         _check(load().pot3d_last_stats(self.h, ctypes.byref(s)), "pot3d_last_stats")
         return {"status": s.status, "iters": s.iters, "outer_iters": s.outer_iters,
-                "relres": s.relres, "kernel_ms": list(s.kernel_ms)}
+                "relres": s.relres, "kernel_ms": list(s.kernel_ms), "launches": s.launches}
 
     def _bind_stream(self, *arrays):
         st = _stream_of(*arrays)
