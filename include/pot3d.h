@@ -55,6 +55,7 @@ extern "C" {
 #define POT3D_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up          */
 #define POT3D_ERR_UNSUPPORTED (-7)  /* option not implemented                      */
 #define POT3D_ERR_BUSY (-8)         /* batch full / no memory to admit now         */
+#define POT3D_ERR_TOO_LARGE (-9)    /* request needs more than a fixed-size buffer */
 
 /* ---- arithmetic of the PCG iteration ------------------------------- */
 #define POT3D_PREC_FP64 0    /* every operation in native FP64                      */
@@ -176,6 +177,25 @@ int pot3d_apply(pot3d_plan_t *plan, const double *x, double *y);
 
 /* FP64 relative residual ||b(Br) - L phi|| / ||b(Br)||. br, phi dev or host. */
 int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, double *relres);
+
+/* The same residual as pot3d_residual for callers that cannot allocate
+ * device memory during the call (device memory owned by another allocator,
+ * a fixed memory budget, or code where an allocation would synchronise the
+ * device).  The paper has no counterpart; this is a library convenience.
+ *   br [nt*np], phi [nr*nt*np]   device pointers only (host arrays would need
+ *                                a staging copy: POT3D_ERR_INVALID_ARG)
+ *   relres                       host, written
+ * Allocates nothing: the plan (created beforehand) supplies its tables, and
+ * the per-block partial sums go to a 32 KiB scratch array compiled into the
+ * library (4096 doubles, room for 2047 blocks; the call launches at most
+ * 4 x SMs blocks and returns POT3D_ERR_TOO_LARGE if that exceeds the room).
+ * Every GPU that loads the library holds the array until the process exits.
+ * The first call on each device looks up the array's device address, so it
+ * should come before any stream capture.  All calls share the array: calls
+ * whose kernels overlap on the GPU race; order them on one stream.  The
+ * result agrees with pot3d_residual to rounding. */
+int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, const double *phi,
+                           double *relres);
 
 int pot3d_last_error(void);
 const char *pot3d_strerror(int code);

@@ -278,6 +278,7 @@ const char *pot3d_strerror(int code) {
   case POT3D_ERR_TIMEOUT: return "device-side wait timed out";
   case POT3D_ERR_UNSUPPORTED: return "unsupported option";
   case POT3D_ERR_BUSY: return "no room to admit the request now";
+  case POT3D_ERR_TOO_LARGE: return "request needs more than a fixed-size buffer holds";
   default: return "unknown error";
   }
 }

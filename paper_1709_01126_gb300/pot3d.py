@@ -24,6 +24,7 @@ POT3D_ERR_BREAKDOWN = -5
 POT3D_ERR_TIMEOUT = -6
 POT3D_ERR_UNSUPPORTED = -7
 POT3D_ERR_BUSY = -8
+POT3D_ERR_TOO_LARGE = -9
 
 POT3D_PREC_FP64 = 0
 POT3D_PREC_FP64_DF = 1
@@ -67,7 +68,7 @@ class pot3d_info_t(ctypes.Structure):
 EXPORTS = ["pot3d_plan", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
            "pot3d_last_stats", "pot3d_workspace_bytes", "pot3d_set_workspace", "pot3d_solve",
            "pot3d_solve_mixed", "pot3d_field", "pot3d_apply", "pot3d_residual",
-           "pot3d_last_error", "pot3d_strerror"]
+           "pot3d_residual_noalloc", "pot3d_last_error", "pot3d_strerror"]
 
 _lib = None
 
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = False):
     L.pot3d_field.argtypes = [P, V, V, V]
     L.pot3d_apply.argtypes = [P, V, V]
     L.pot3d_residual.argtypes = [P, V, V, D]
+    L.pot3d_residual_noalloc.argtypes = [P, V, V, D]
     L.pot3d_last_error.argtypes = []
     L.pot3d_strerror.argtypes = [I]
     L.pot3d_strerror.restype = ctypes.c_char_p
@@ -254,6 +256,16 @@ class Plan:
         _check(load().pot3d_residual(self.h, _ptr(br), _ptr(phi), ctypes.byref(r)),
                "pot3d_residual")
         return r.value
+
+    def residual_noalloc(self, br, phi, check=True):
+        """pot3d_residual_noalloc: device arrays only; allocates nothing."""
+        self._bind_stream(br, phi)
+        r = ctypes.c_double(0.0)
+        rc = load().pot3d_residual_noalloc(self.h, _ptr(br), _ptr(phi), ctypes.byref(r))
+        if check:
+            _check(rc, "pot3d_residual_noalloc")
+            return r.value
+        return rc, r.value
 
     def field_sizes(self):
         nr, nt, np_ = self.shape
