@@ -197,6 +197,39 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
 int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, const double *phi,
                            double *relres);
 
+/* ---- batched solves (continuous batching) ------------------------------
+ * Many solves of different grids advance together in the same persistent
+ * kernels: each admitted solve runs the arithmetic of pot3d_solve_mixed
+ * (FP32 PCG inside FP64 refinement, the plan's tile decomposition and its own
+ * fixed-order reductions, so its result is bitwise the same as
+ * pot3d_solve_mixed on the same plan, alone or in any mix).
+ * pot3d_batch_create: max_bytes of device arena (allocated once) and up to
+ *   max_slots concurrent solves.  NULL on error (pot3d_last_error()).
+ * pot3d_batch_submit: admits a solve if a slot and arena memory are free
+ *   (else POT3D_ERR_BUSY, nothing changed).  br [nt*np] and phi [nr*nt*np]
+ *   are device pointers that must stay valid until the solve is polled;
+ *   phi receives the solution.  The plan may be shared by many solves.
+ * pot3d_batch_step: advances every admitted solve by up to k inner
+ *   iterations (one CUDA graph of k iterations) and runs the refinement
+ *   step of those whose inner solve stopped.  Returns the number of solves
+ *   still running, or an error.
+ * pot3d_batch_poll: retires up to max finished solves, writing their tag,
+ *   status, refinement steps, inner iterations and final FP64 relative
+ *   residual (any output pointer may be NULL), and frees their memory.
+ * One batch must not be used from two host threads at once. */
+typedef struct pot3d_batch pot3d_batch_t;
+pot3d_batch_t *pot3d_batch_create(size_t max_bytes, int max_slots);
+void pot3d_batch_destroy(pot3d_batch_t *batch);
+int pot3d_batch_set_stream(pot3d_batch_t *batch, void *cuda_stream);
+int pot3d_batch_set_opts(pot3d_batch_t *batch, const pot3d_opts_t *opts);
+size_t pot3d_batch_bytes_needed(pot3d_batch_t *batch, const pot3d_plan_t *plan);
+int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *br, double tol,
+                       double *phi, long long tag);
+int pot3d_batch_step(pot3d_batch_t *batch, int k);
+int pot3d_batch_poll(pot3d_batch_t *batch, long long *tags, int *status, int *outer_iters,
+                     int *inner_iters, double *relres, int max, int *n_done);
+int pot3d_batch_info(pot3d_batch_t *batch, int *active, size_t *bytes_used, size_t *bytes_cap);
+
 int pot3d_last_error(void);
 const char *pot3d_strerror(int code);
 

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(NT) k_sum_pairs(const double *part, int n, dou
 // tiny residuals inside the float range of the double-float arithmetic).
 // With x0, sums[2], sums[3] hold ||r0||^2 and sum Dinv r0^2 of the unscaled
 // initial residual.
-__global__ void k_start(SolveState *st, const double *sums, double n0, double tol, int maxit,
+static __global__ void k_start(SolveState *st, const double *sums, double n0, double tol, int maxit,
                         int use_x0, double forced_scale) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double bb = sums[0];
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT)
 }
 
 // Refinement update x64 += Dinv (x~32 + alpha p~32) / scale (FP64).
-__global__ void k_refine_update(const ProbDev *probs, const double *__restrict__ c64,
+static __global__ void k_refine_update(const ProbDev *probs, const double *__restrict__ c64,
                                 double *x64, double inv_scale) {
   const ProbDev &P = probs[0];
   const SolveState *st = P.st;
@@ -249,7 +249,7 @@ __global__ void k_refine_update(const ProbDev *probs, const double *__restrict__
 }
 
 // Copy a padded FP64 vector to the dense layout (and back).
-__global__ void k_unpad(const double *__restrict__ src, int spitch, double *__restrict__ dst,
+static __global__ void k_unpad(const double *__restrict__ src, int spitch, double *__restrict__ dst,
                         int dpitch, size_t rows, int np) {
   const size_t n = rows * np;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
@@ -287,7 +287,7 @@ struct FieldTabs {
 };
 
 // B = grad Phi on the staggered faces; see the header for the layout.
-__global__ void k_field(const double *__restrict__ phi, const double *__restrict__ br,
+static __global__ void k_field(const double *__restrict__ phi, const double *__restrict__ br,
                         const double *__restrict__ poles, FieldTabs T, int nr, int nt, int np,
                         double *__restrict__ B) {
   const size_t nrf = (size_t)(nr + 1) * nt * np;

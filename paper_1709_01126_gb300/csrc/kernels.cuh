@@ -201,7 +201,8 @@ struct MvLayout {
 // registers).  The sigma partial closes with the last-block reduction.
 template <class A, int TJ, int VK, int S>
 __global__ void __launch_bounds__(32 * TJ, 3)
-    k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work, int nwork) {
+    k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
+             const int *__restrict__ nwork_p) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
@@ -220,6 +221,9 @@ __global__ void __launch_bounds__(32 * TJ, 3)
   __syncthreads();
   uint32_t seq = 0; // planes consumed by this block so far (stage/parity counter)
 
+  // the work list (and its length) lives in device memory, so one captured
+  // graph serves any batch composition
+  const int nwork = __ldcg(nwork_p);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
     const ProbDev &P = probs[wi.x];
@@ -456,7 +460,8 @@ __global__ void __launch_bounds__(32 * TJ, 3)
 // ||r||^2 += s and rho += D^-1 s.  The last block closes the iteration.
 template <class A, int NT>
 __global__ void __launch_bounds__(NT, 3)
-    k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work, int nwork) {
+    k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
+             const int *__restrict__ nwork_p) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
@@ -464,6 +469,7 @@ __global__ void __launch_bounds__(NT, 3)
   __shared__ double red[NW];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, tid = threadIdx.x;
+  const int nwork = __ldcg(nwork_p);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
     const ProbDev &P = probs[wi.x];

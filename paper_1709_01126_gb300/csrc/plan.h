@@ -48,6 +48,7 @@ struct Plan {
   // work decomposition
   int nJ = 0, nK = 0, ic = 0, nI = 0, tiles_a = 0, rows_b = 0, tiles_b = 0;
   int2 *d_work_a = nullptr, *d_work_b = nullptr;
+  int *d_nwork = nullptr; // [tiles_a, tiles_b] on the device
   ArithData ar[3];
   // workspace (vectors)
   char *ws = nullptr;
@@ -83,5 +84,8 @@ double *ws_x64(const Plan *P);
 double *ws_r64(const Plan *P);
 int stage(Plan *P, size_t bytes);
 void scaled_table(const Plan *P, std::vector<double> &t);
+int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by);
+int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P);
+int default_maxit(const Plan *P);
 
 } // namespace pot3d

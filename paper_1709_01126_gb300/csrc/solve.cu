@@ -52,6 +52,9 @@ int plan_device_init(Plan *P) {
   CTRY(cudaMalloc(&P->d_work_b, sizeof(int2) * wb.size()));
   CTRY(cudaMemcpy(P->d_work_a, wa.data(), sizeof(int2) * wa.size(), cudaMemcpyHostToDevice));
   CTRY(cudaMemcpy(P->d_work_b, wb.data(), sizeof(int2) * wb.size(), cudaMemcpyHostToDevice));
+  const int counts[2] = {P->tiles_a, P->tiles_b};
+  CTRY(cudaMalloc(&P->d_nwork, sizeof(counts)));
+  CTRY(cudaMemcpy(P->d_nwork, counts, sizeof(counts), cudaMemcpyHostToDevice));
   auto up = [](double **d, const std::vector<double> &h) -> cudaError_t {
     cudaError_t e = cudaMalloc((void **)d, sizeof(double) * h.size());
     if (e != cudaSuccess) return e;
@@ -88,6 +91,7 @@ void plan_free(Plan *P) {
   for (auto e : P->ev) cudaEventDestroy(e);
   cudaFree(P->d_work_a);
   cudaFree(P->d_work_b);
+  cudaFree(P->d_nwork);
   cudaFree(P->d_c64);
   cudaFree(P->d_S);
   cudaFree(P->d_irs);
@@ -130,12 +134,12 @@ static int matvec_smem_setup() {
 template <class A>
 static void launch_matvec(Plan *P, int ai) {
   k_matvec<A, kTJ, kVK, MvCfg<A>::S><<<P->tiles_a, dim3(32, kTJ), MvCfg<A>::LY::BYTES, P->stream>>>(
-      P->ar[ai].d_prob, P->d_work_a, P->tiles_a);
+      P->ar[ai].d_prob, P->d_work_a, P->d_nwork);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
 // link-time dependency on libcuda).
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
   if (!tried) {
@@ -152,7 +156,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 3-D map over a padded vector [nr][nt][pitch] with a (bx, by, 1) box.
-static int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by) {
+int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return POT3D_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)P->pitch, (cuuint64_t)P->nt, (cuuint64_t)P->nr};
@@ -164,6 +168,21 @@ static int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, i
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? POT3D_OK : POT3D_ERR_CUDA;
+}
+
+// metric table [6][nr][ntp]: box of kTJ theta rows x 1 plane x 6 tables
+int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return POT3D_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)P->ntp, (cuuint64_t)P->nr, 6u};
+  cuuint64_t strides[2] = {(cuuint64_t)P->ntp * es, (cuuint64_t)P->nr * P->ntp * es};
+  cuuint32_t box[3] = {(cuuint32_t)kTJ, 1u, 6u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult cr = fn(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                   const_cast<void *>(coef), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS ? POT3D_OK : POT3D_ERR_CUDA;
 }
 
 template <class A>
@@ -180,20 +199,7 @@ static int build_tma(Plan *P, int ai) {
   if (!rc) rc = encode3d(&T.rw, h.r, es, P, LY::AL, LY::RH);
   if (!rc) rc = encode3d(&T.p0w, h.p0, es, P, LY::AL, LY::RH);
   if (!rc) rc = encode3d(&T.p1w, h.p1, es, P, LY::AL, LY::RH);
-  if (!rc) {
-    // metric table [6][nr][ntp]: box of kTJ theta rows x 1 plane x 6 tables
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    cuuint64_t dims[3] = {(cuuint64_t)P->ntp, (cuuint64_t)P->nr, 6u};
-    cuuint64_t strides[2] = {(cuuint64_t)P->ntp * es, (cuuint64_t)P->nr * P->ntp * es};
-    cuuint32_t box[3] = {(cuuint32_t)kTJ, 1u, 6u};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult cr = fn ? fn(&T.cf, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
-                          3, D.coef, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE)
-                     : CUDA_ERROR_NOT_FOUND;
-    if (cr != CUDA_SUCCESS) rc = POT3D_ERR_CUDA;
-  }
+  if (!rc) rc = encode_coef_map(&T.cf, D.coef, es, P);
   if (rc) return rc;
   if (!D.d_tma) {
     if (cudaMalloc(&D.d_tma, sizeof(TmaSet)) != cudaSuccess) {
@@ -209,7 +215,7 @@ static int build_tma(Plan *P, int ai) {
 template <class A>
 static void launch_update(Plan *P, int ai) {
   k_update<A, kUpdThreads><<<P->tiles_b, kUpdThreads, 0, P->stream>>>(P->ar[ai].d_prob,
-                                                                       P->d_work_b, P->tiles_b);
+                                                                       P->d_work_b, P->d_nwork + 1);
 }
 
 static int auto_chunk(const Plan *P, int ai) {
@@ -334,7 +340,7 @@ static int status_code(int st) {
   }
 }
 
-static int default_maxit(const Plan *P) { return 100 * (P->nr + P->nt + P->np); }
+int default_maxit(const Plan *P) { return 100 * (P->nr + P->nt + P->np); }
 
 // Inputs may be host or device pointers; host arrays are staged through
 // one device buffer [br | phi | B].

@@ -68,7 +68,10 @@ class pot3d_info_t(ctypes.Structure):
 EXPORTS = ["pot3d_plan", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
            "pot3d_last_stats", "pot3d_workspace_bytes", "pot3d_set_workspace", "pot3d_solve",
            "pot3d_solve_mixed", "pot3d_field", "pot3d_apply", "pot3d_residual",
-           "pot3d_residual_noalloc", "pot3d_last_error", "pot3d_strerror"]
+           "pot3d_residual_noalloc", "pot3d_batch_create", "pot3d_batch_destroy",
+           "pot3d_batch_set_stream", "pot3d_batch_set_opts", "pot3d_batch_bytes_needed",
+           "pot3d_batch_submit", "pot3d_batch_step", "pot3d_batch_poll", "pot3d_batch_info",
+           "pot3d_last_error", "pot3d_strerror"]
 
 _lib = None
 
@@ -107,6 +110,20 @@ def load(build_if_missing: bool = False):
     L.pot3d_apply.argtypes = [P, V, V]
     L.pot3d_residual.argtypes = [P, V, V, D]
     L.pot3d_residual_noalloc.argtypes = [P, V, V, D]
+    L.pot3d_batch_create.argtypes = [ctypes.c_size_t, I]
+    L.pot3d_batch_create.restype = P
+    L.pot3d_batch_destroy.argtypes = [P]
+    L.pot3d_batch_destroy.restype = None
+    L.pot3d_batch_set_stream.argtypes = [P, V]
+    L.pot3d_batch_set_opts.argtypes = [P, ctypes.POINTER(pot3d_opts_t)]
+    L.pot3d_batch_bytes_needed.argtypes = [P, P]
+    L.pot3d_batch_bytes_needed.restype = ctypes.c_size_t
+    L.pot3d_batch_submit.argtypes = [P, P, V, ctypes.c_double, V, ctypes.c_longlong]
+    L.pot3d_batch_step.argtypes = [P, I]
+    L.pot3d_batch_poll.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I),
+                                   ctypes.POINTER(I), ctypes.POINTER(I), D, I, ctypes.POINTER(I)]
+    L.pot3d_batch_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_size_t)]
     L.pot3d_last_error.argtypes = []
     L.pot3d_strerror.argtypes = [I]
     L.pot3d_strerror.restype = ctypes.c_char_p
@@ -270,6 +287,69 @@ class Plan:
     def field_sizes(self):
         nr, nt, np_ = self.shape
         return ((nr + 1) * nt * np_, nr * (nt + 1) * np_, nr * nt * np_)
+
+
+class Batch:
+    """Owns a pot3d_batch_t (continuous batching of mixed-precision solves)."""
+
+    def __init__(self, max_bytes: int, max_slots: int = 256, inner_tol=0.0, max_outer=0,
+                 max_iters=0):
+        L = load()
+        h = L.pot3d_batch_create(int(max_bytes), int(max_slots))
+        if not h:
+            raise Pot3dError(L.pot3d_last_error(), "pot3d_batch_create")
+        self.h = h
+        self.max_slots = int(max_slots)
+        o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer))
+        _check(L.pot3d_batch_set_opts(h, ctypes.byref(o)), "pot3d_batch_set_opts")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pot3d_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        _check(load().pot3d_batch_set_stream(self.h, stream_handle), "pot3d_batch_set_stream")
+
+    def bytes_needed(self, plan: "Plan") -> int:
+        return int(load().pot3d_batch_bytes_needed(self.h, plan.h))
+
+    def submit(self, plan: "Plan", br, tol, phi, tag: int) -> bool:
+        """True if admitted, False if busy (no slot or memory)."""
+        rc = load().pot3d_batch_submit(self.h, plan.h, _ptr(br), float(tol), _ptr(phi), int(tag))
+        if rc == POT3D_ERR_BUSY:
+            return False
+        _check(rc, "pot3d_batch_submit")
+        return True
+
+    def step(self, k: int) -> int:
+        rc = load().pot3d_batch_step(self.h, int(k))
+        if rc < 0:
+            raise Pot3dError(rc, "pot3d_batch_step")
+        return rc
+
+    def poll(self, max_n: int = 1024):
+        """List of (tag, status, outer, inner, relres) of retired solves."""
+        n = max(1, min(max_n, self.max_slots))
+        tags = (ctypes.c_longlong * n)()
+        st, o, i = (ctypes.c_int * n)(), (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        rr = (ctypes.c_double * n)()
+        nd = ctypes.c_int(0)
+        _check(load().pot3d_batch_poll(self.h, tags, st, o, i, rr, n, ctypes.byref(nd)),
+               "pot3d_batch_poll")
+        return [(tags[u], st[u], o[u], i[u], rr[u]) for u in range(nd.value)]
+
+    def info(self):
+        a, u, c = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(load().pot3d_batch_info(self.h, ctypes.byref(a), ctypes.byref(u), ctypes.byref(c)),
+               "pot3d_batch_info")
+        return {"active": a.value, "bytes_used": u.value, "bytes_cap": c.value}
 
 
 # C-named entry points (argument marshalling only)
