@@ -362,6 +362,41 @@ def run_gpu(args):
     return 0
 
 
+def run_serve(args):
+    """Serving stream: seeded Poisson arrivals of solves on grids drawn from
+    41x61x121, 81x121x241, 101x181x361 and 151x301x601 (bipole Br with seed
+    1709 + request id, tol 1e-10), served by the continuous-batching mixed
+    path and by FP64 one-at-a-time solves on the same trace.  The arrival rate
+    is 1.5x the calibrated FP64 one-at-a-time solve rate over the grid mix."""
+    import torch
+
+    from paper_1709_01126_gb300 import pot3d, serve
+
+    pot3d.load()
+    rate64, times = serve.calibrate_fp64_rate()
+    rate = 1.5 * rate64
+    reqs = serve.make_requests(args.requests, rate)
+    inputs = serve.prepare_inputs(reqs)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(0.5 * free, 96e9))
+    batched = serve.run_batched(reqs, inputs, batch_bytes=budget, k=args.batch_k,
+                                inner_tol=args.inner_tol)
+    base = serve.run_fp64_serial(reqs, inputs)
+    b, f = batched.summary(), base.summary()
+    line = {"metric": METRIC, "value": b["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "workload_kind": "serve",
+            "config": {"workload": "serving stream of %d solves, Poisson arrivals at %.3f/s "
+                                   "(1.5x FP64 rate), grids %s, tol 1e-10"
+                                   % (args.requests, rate, serve.GRIDS),
+                       "batch_arena_bytes": budget, "step_iters": args.batch_k},
+            "batched": b, "fp64_one_at_a_time": f,
+            "speedup_solves_per_s": b["solves_per_s"] / f["solves_per_s"],
+            "fp64_calibration_s": dict(zip(["x".join(map(str, g)) for g in serve.GRIDS], times))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Short solve for ncu: the same 151x301x601 problem, capped at a few
     PCG iterations so a capture ends quickly."""
@@ -398,6 +433,10 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
+    ap.add_argument("--workload", default="pcg", choices=["pcg", "serve"])
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--batch-k", type=int, default=16)
+    ap.add_argument("--inner-tol", type=float, default=0.0)
     args = ap.parse_args()
     args.variants = [v for v in args.variants.split(",") if v]
     if args.profile_case:
@@ -406,6 +445,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 
