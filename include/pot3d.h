@@ -137,6 +137,18 @@ int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *opts);
 int pot3d_get_info(const pot3d_plan_t *plan, pot3d_info_t *info);
 int pot3d_last_stats(const pot3d_plan_t *plan, pot3d_stats_t *stats);
 
+/* Autotuner: times every matvec tile-shape variant and r-chunk count of the
+ * selected arithmetics on this plan's problem (a few launches each, on the
+ * plan's stream, with the plan's workspace) and keeps the fastest for later
+ * solves.  flags: bit 0 FP64, bit 1 double-float, bit 2 FP32 (the inner
+ * solve of refinement and batches); 0 = the plan's own precision.  Results
+ * are cached per (nr, nt, np, arithmetic) for the process and, when the
+ * environment names a file in POT3D_TUNE_CACHE, across processes.
+ * variant / chunks / ms (may be NULL) receive the choice for the last
+ * arithmetic tuned: variant index, r-chunks per tile column, and the matvec
+ * time in ms measured when the choice was made. */
+int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *chunks, double *ms);
+
 /* Device workspace.  By default the plan allocates it with cudaMalloc at
  * the first solve.  A caller that manages device memory itself passes a
  * buffer of at least pot3d_workspace_bytes() bytes, 256-byte aligned; it

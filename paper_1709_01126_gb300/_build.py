@@ -12,8 +12,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
-OUT_DIR = os.path.join(PKG, "_build")
+OUT_DIR = os.environ.get("POT3D_BUILD_DIR") or os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libpot3d.so")
+# extra nvcc flags, e.g. "-DPOT3D_VK=4" for another matvec tile shape
+EXTRA = os.environ.get("POT3D_NVCC_FLAGS", "").split()
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
 
@@ -49,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + EXTRA + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)

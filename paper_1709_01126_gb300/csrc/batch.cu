@@ -111,9 +111,11 @@ struct pot3d_batch {
   double *h_sums = nullptr;
   std::vector<ProbDev> h_probs;
   std::vector<TmaSet> h_tmas;
-  int2 *d_work = nullptr; // [2][cap]: matvec items then update items
-  int *d_nwork = nullptr;
+  int n_var = 0;          // FP32 matvec variants
+  int2 *d_work = nullptr; // [n_var + 1][cap]: matvec items per variant, then update items
+  int *d_nwork = nullptr; // [n_var + 1]
   int work_cap = 0;
+  unsigned var_mask = 0, graph_mask = 0; // variants with work now / in the graph
   bool dirty = true;
   cudaStream_t stream = nullptr, own_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -132,39 +134,39 @@ int grid_for(const Batch *B, size_t n) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)4 * B->nsm));
 }
 
+// Arena bytes of one solve: FP32 x~, r, p~0, p~1, q; FP64 x64, r64; the
+// partial slots of its matvec and update items and of its FP64 reductions.
 size_t slot_bytes(const Plan *P, int nsm) {
+  const ArithData &D = P->ar[AR_F32];
   const size_t v4 = al(P->npad * 4), v8 = al(P->npad * 8);
-  return 5 * v4 + 2 * v8 + al(sizeof(double) * P->tiles_a) + al(sizeof(double) * 2 * P->tiles_b) +
+  return 5 * v4 + 2 * v8 + al(sizeof(double) * D.tiles_a) + al(sizeof(double) * 2 * D.tiles_b) +
          al(sizeof(double) * 2 * 4 * nsm);
 }
 
-int smem_setup_f32() {
-  static int done = 0;
-  if (!done) {
-    using LY = MvLayout<4, kTJ, kVK, kStages4>;
-    cudaError_t e = cudaFuncSetAttribute(k_matvec<PF32, kTJ, kVK, kStages4>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
-    if (e != cudaSuccess) return cuda_status(e);
-    done = 1;
-  }
-  return POT3D_OK;
-}
-
-// Rebuild and upload the concatenated work lists of the occupied slots.
+// Rebuild and upload the concatenated work lists of the occupied slots:
+// one matvec list per FP32 variant (each slot uses its plan's variant) and
+// one update list.
 int rebuild_work(Batch *B) {
-  std::vector<int2> wa, wb;
+  const int nl = B->n_var + 1;
+  std::vector<std::vector<int2>> lists(nl);
   for (int s = 0; s < B->max_slots; s++) {
     const Slot &S = B->slots[s];
     if (S.phase == PH_FREE || S.phase == PH_DONE) continue;
-    for (int t = 0; t < S.plan->tiles_a; t++) wa.push_back(make_int2(s, t));
-    for (int t = 0; t < S.plan->tiles_b; t++) wb.push_back(make_int2(s, t));
+    const ArithData &D = S.plan->ar[AR_F32];
+    for (int t = 0; t < D.tiles_a; t++) lists[D.var].push_back(make_int2(s, t));
+    for (int t = 0; t < D.tiles_b; t++) lists[B->n_var].push_back(make_int2(s, t));
   }
-  const int need = (int)std::max(wa.size(), wb.size());
-  if (need > B->work_cap) {
+  size_t need = 0;
+  unsigned mask = 0;
+  for (int v = 0; v < nl; v++) {
+    need = std::max(need, lists[v].size());
+    if (v < B->n_var && !lists[v].empty()) mask |= 1u << v;
+  }
+  if ((int)need > B->work_cap) {
     // grow before any graph uses the old list; the graph is re-captured
     if (B->d_work) cudaFree(B->d_work);
-    B->work_cap = std::max(need, 2 * B->work_cap);
-    if (cudaMalloc(&B->d_work, sizeof(int2) * 2 * B->work_cap) != cudaSuccess) {
+    B->work_cap = std::max((int)need, 2 * B->work_cap);
+    if (cudaMalloc(&B->d_work, sizeof(int2) * nl * B->work_cap) != cudaSuccess) {
       cudaGetLastError();
       B->work_cap = 0;
       B->d_work = nullptr;
@@ -173,29 +175,38 @@ int rebuild_work(Batch *B) {
     if (B->graph) cudaGraphExecDestroy(B->graph);
     B->graph = nullptr;
   }
-  std::vector<int2> all(2 * (size_t)B->work_cap, make_int2(0, 0));
-  std::copy(wa.begin(), wa.end(), all.begin());
-  std::copy(wb.begin(), wb.end(), all.begin() + B->work_cap);
-  const int counts[2] = {(int)wa.size(), (int)wb.size()};
-  // synchronous copies from pageable memory: the step's graph is ordered after
+  std::vector<int2> all((size_t)nl * B->work_cap, make_int2(0, 0));
+  std::vector<int> counts(nl);
+  for (int v = 0; v < nl; v++) {
+    std::copy(lists[v].begin(), lists[v].end(), all.begin() + (size_t)v * B->work_cap);
+    counts[v] = (int)lists[v].size();
+  }
   if (B->work_cap &&
       cudaMemcpyAsync(B->d_work, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice,
                       B->stream) != cudaSuccess)
     return POT3D_ERR_CUDA;
-  if (cudaMemcpyAsync(B->d_nwork, counts, sizeof(counts), cudaMemcpyHostToDevice, B->stream) !=
-      cudaSuccess)
+  if (cudaMemcpyAsync(B->d_nwork, counts.data(), sizeof(int) * nl, cudaMemcpyHostToDevice,
+                      B->stream) != cudaSuccess)
     return POT3D_ERR_CUDA;
+  // the host vectors above are pageable and local: finish the copies here
   if (cudaStreamSynchronize(B->stream) != cudaSuccess) return POT3D_ERR_CUDA;
+  B->var_mask = mask;
   B->dirty = false;
   return POT3D_OK;
 }
 
+// One iteration of every running slot: the matvec of each variant present,
+// then the update, all persistent (a few blocks per SM looping over items).
 void launch_iteration(Batch *B) {
-  using LY = MvLayout<4, kTJ, kVK, kStages4>;
-  k_matvec<PF32, kTJ, kVK, kStages4><<<3 * B->nsm, dim3(32, kTJ), LY::BYTES, B->stream>>>(
-      B->d_probs, B->d_work, B->d_nwork);
-  k_update<PF32, kUpdThreads><<<3 * B->nsm, kUpdThreads, 0, B->stream>>>(
-      B->d_probs, B->d_work + B->work_cap, B->d_nwork + 1);
+  int nv = 0;
+  const MvVariant *vs = mv_variants(AR_F32, &nv);
+  for (int v = 0; v < B->n_var; v++) {
+    if (!(B->graph_mask & (1u << v))) continue;
+    vs[v].launch(B->d_probs, B->d_work + (size_t)v * B->work_cap, B->d_nwork + v,
+                 vs[v].blocks_per_sm * B->nsm, B->stream);
+  }
+  update_launcher(AR_F32)(B->d_probs, B->d_work + (size_t)B->n_var * B->work_cap,
+                          B->d_nwork + B->n_var, 3 * B->nsm, B->stream);
 }
 
 // FP64 residual r64 = b - L x64 of slot s and its sums (into d_sums[s][2..3]).
@@ -327,13 +338,17 @@ pot3d_batch_t *pot3d_batch_create(size_t max_bytes, int max_slots) {
             cudaMalloc(&B->d_tmas, sizeof(TmaSet) * max_slots) == cudaSuccess &&
             cudaMalloc(&B->d_sums, sizeof(double) * 4 * max_slots) == cudaSuccess &&
             cudaMalloc(&B->d_isums, sizeof(double) * 2 * max_slots) == cudaSuccess &&
-            cudaMalloc(&B->d_nwork, sizeof(int) * 2) == cudaSuccess &&
+            cudaMalloc(&B->d_nwork, sizeof(int) * 8) == cudaSuccess &&
             cudaMallocHost(&B->h_states, sizeof(SolveState) * max_slots) == cudaSuccess &&
             cudaMallocHost(&B->h_sums, sizeof(double) * 4 * max_slots) == cudaSuccess;
   if (ok) {
     B->stream = B->own_stream;
     ok = cudaMemset(B->d_states, 0, sizeof(SolveState) * max_slots) == cudaSuccess &&
-         cudaMemset(B->d_nwork, 0, sizeof(int) * 2) == cudaSuccess && smem_setup_f32() == POT3D_OK;
+         cudaMemset(B->d_nwork, 0, sizeof(int) * 8) == cudaSuccess;
+    int nv = 0;
+    const MvVariant *vs = mv_variants(AR_F32, &nv);
+    B->n_var = nv;
+    for (int v = 0; v < nv && ok; v++) ok = vs[v].setup() == 0;
   }
   if (!ok) {
     cudaGetLastError();
@@ -383,7 +398,9 @@ int pot3d_batch_set_opts(pot3d_batch_t *batch, const pot3d_opts_t *o) {
 
 size_t pot3d_batch_bytes_needed(pot3d_batch_t *batch, const pot3d_plan_t *plan) {
   if (!batch || !plan) return 0;
-  return slot_bytes(reinterpret_cast<const Plan *>(plan), reinterpret_cast<Batch *>(batch)->nsm);
+  Plan *P = reinterpret_cast<Plan *>(const_cast<pot3d_plan_t *>(plan));
+  if (ensure_arith(P, AR_F32)) return 0;
+  return slot_bytes(P, reinterpret_cast<Batch *>(batch)->nsm);
 }
 
 int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *br, double tol,
@@ -400,14 +417,12 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
       break;
     }
   if (s < 0) return POT3D_ERR_BUSY;
+  int rc = ensure_arith(P, AR_F32);
+  if (rc) return fail(rc);
+  const ArithData &D = P->ar[AR_F32];
   const size_t bytes = slot_bytes(P, B->nsm);
   const size_t off = B->arena.alloc(bytes);
   if (off == SIZE_MAX) return POT3D_ERR_BUSY;
-  int rc = ensure_arith(P, AR_F32);
-  if (rc) {
-    B->arena.release(off, bytes);
-    return fail(rc);
-  }
   Slot &S = B->slots[s];
   S = Slot{};
   S.phase = PH_START;
@@ -426,9 +441,9 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   S.r64 = reinterpret_cast<double *>(p + v8);
   p += 2 * v8;
   S.part_a = reinterpret_cast<double *>(p);
-  p += al(sizeof(double) * P->tiles_a);
+  p += al(sizeof(double) * D.tiles_a);
   S.part_b = reinterpret_cast<double *>(p);
-  p += al(sizeof(double) * 2 * P->tiles_b);
+  p += al(sizeof(double) * 2 * D.tiles_b);
   S.part_aux = reinterpret_cast<double *>(p);
   // descriptor and TMA maps of the slot
   ProbDev &h = B->h_probs[s];
@@ -438,13 +453,13 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   h.np = P->np;
   h.pitch = P->pitch;
   h.ntp = P->ntp;
-  h.nJ = P->nJ;
-  h.nK = P->nK;
-  h.ic = P->ic;
-  h.nI = P->nI;
-  h.tiles_a = P->tiles_a;
-  h.rows_b = P->rows_b;
-  h.tiles_b = P->tiles_b;
+  h.nJ = D.nJ;
+  h.nK = D.nK;
+  h.ic = D.ic;
+  h.nI = D.nI;
+  h.tiles_a = D.tiles_a;
+  h.rows_b = D.rows_b;
+  h.tiles_b = D.tiles_b;
   h.plane = (long long)P->nt * P->pitch;
   h.x = S.v32[0];
   h.r = S.v32[1];
@@ -456,16 +471,9 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   h.part_b = S.part_b;
   h.st = B->d_states + s;
   h.tma = B->d_tmas + s;
-  using LY = MvLayout<4, kTJ, kVK, kStages4>;
   TmaSet &T = B->h_tmas[s];
-  rc = encode3d(&T.r, h.r, 4, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.p0, h.p0, 4, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.p1, h.p1, 4, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.x, h.x, 4, P, LY::TK, kTJ);
-  if (!rc) rc = encode3d(&T.rw, h.r, 4, P, LY::AL, LY::RH);
-  if (!rc) rc = encode3d(&T.p0w, h.p0, 4, P, LY::AL, LY::RH);
-  if (!rc) rc = encode3d(&T.p1w, h.p1, 4, P, LY::AL, LY::RH);
-  if (!rc) rc = encode_coef_map(&T.cf, h.coef, 4, P);
+  int nv = 0;
+  rc = encode_tma_set(&T, h, h.coef, mv_variants(AR_F32, &nv)[D.var], P);
   cudaStream_t st = B->stream;
   if (!rc && (cudaMemcpyAsync(B->d_probs + s, &h, sizeof(ProbDev), cudaMemcpyHostToDevice, st) !=
                   cudaSuccess ||
@@ -511,7 +519,8 @@ int pot3d_batch_step(pot3d_batch_t *batch, int k) {
   int running = 0;
   for (const Slot &S : B->slots) running += (S.phase == PH_INNER);
   if (running) {
-    if (!B->graph || B->graph_k != k) {
+    if (!B->graph || B->graph_k != k || B->graph_mask != B->var_mask) {
+      B->graph_mask = B->var_mask;
       if (B->graph) cudaGraphExecDestroy(B->graph);
       B->graph = nullptr;
       cudaGraph_t g;

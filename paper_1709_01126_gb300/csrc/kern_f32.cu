@@ -1,0 +1,33 @@
+// FP32 instantiations of the iteration kernels (inner solve of refinement).
+#include "kern_inst.cuh"
+
+namespace pot3d {
+
+const MvVariant *mv_variants_f32(int *count) {
+  static const MvVariant v[] = {make_variant<PF32, 4, 4, 3>(4), make_variant<PF32, 8, 2, 4>(3),
+                                make_variant<PF32, 8, 4, 3>(2)};
+  *count = 3;
+  return v;
+}
+
+KLaunch update_launcher_f32() { return &up_launch<PF32>; }
+
+// Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
+const MvVariant *mv_variants_f64(int *count);
+const MvVariant *mv_variants_df(int *count);
+KLaunch update_launcher_f64();
+KLaunch update_launcher_df();
+
+const MvVariant *mv_variants(int ai, int *count) {
+  if (ai == 0) return mv_variants_f64(count);
+  if (ai == 1) return mv_variants_df(count);
+  return mv_variants_f32(count);
+}
+
+KLaunch update_launcher(int ai) {
+  if (ai == 0) return update_launcher_f64();
+  if (ai == 1) return update_launcher_df();
+  return update_launcher_f32();
+}
+
+} // namespace pot3d

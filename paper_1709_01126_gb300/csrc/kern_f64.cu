@@ -1,0 +1,14 @@
+// Native FP64 instantiations of the iteration kernels.
+#include "kern_inst.cuh"
+
+namespace pot3d {
+
+const MvVariant *mv_variants_f64(int *count) {
+  static const MvVariant v[] = {make_variant<PF64, 8, 2, 3>(3), make_variant<PF64, 8, 4, 2>(2)};
+  *count = 2;
+  return v;
+}
+
+KLaunch update_launcher_f64() { return &up_launch<PF64>; }
+
+} // namespace pot3d

@@ -1,0 +1,52 @@
+// Instantiation helpers for the per-arithmetic kernel translation units.
+#pragma once
+#include "variants.h"
+
+namespace pot3d {
+
+template <class A, int TJ, int VK, int S>
+int mv_setup() {
+  static int done = 0;
+  if (!done) {
+    using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
+    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, TJ, VK, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
+    if (e != cudaSuccess) return -3; // POT3D_ERR_CUDA
+    done = 1;
+  }
+  return 0;
+}
+
+template <class A, int TJ, int VK, int S>
+void mv_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
+               cudaStream_t s) {
+  using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
+  k_matvec<A, TJ, VK, S><<<grid, dim3(32, TJ), LY::BYTES, s>>>(probs, work, nwork);
+}
+
+template <class A, int TJ, int VK, int S>
+MvVariant make_variant(int blocks_per_sm) {
+  using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
+  MvVariant v;
+  v.tj = TJ;
+  v.vk = VK;
+  v.stages = S;
+  v.es = (int)sizeof(typename A::st);
+  v.al = LY::AL;
+  v.tk = LY::TK;
+  v.rh = LY::RH;
+  v.bw = LY::BW;
+  v.smem_bytes = LY::BYTES;
+  v.blocks_per_sm = blocks_per_sm;
+  v.setup = &mv_setup<A, TJ, VK, S>;
+  v.launch = &mv_launch<A, TJ, VK, S>;
+  return v;
+}
+
+template <class A>
+void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
+               cudaStream_t s) {
+  k_update<A, kUpdThreads><<<grid, kUpdThreads, 0, s>>>(probs, work, nwork);
+}
+
+} // namespace pot3d

@@ -485,6 +485,46 @@ __global__ void __launch_bounds__(NT, 3)
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
     const typename A::scal nalpha = A::scal_from(-ldcg(&stt->alpha[kit & 1]));
     typename A::dacc arr = A::d_init(), arho = A::d_init();
+    if constexpr (A::kFlatUpdate) {
+      // rows [row0, row1) are contiguous (row-major with pitch): stream them
+      // as one flat run of 16-byte vectors, U per thread in flight, and weight
+      // each vector's sum of squares by its row's Dinv
+      constexpr int U = 4;
+      const int vpr = pitch / V; // vectors per row
+      const int nv = (row1 - row0) * vpr;
+      const size_t base = (size_t)row0 * pitch;
+      for (int v0 = tid; v0 < nv; v0 += NT * U) {
+        val rv[U][V], qv[U][V];
+        coef dv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int v = v0 + u * NT;
+          if (v < nv) {
+            A::ldv(r + base + (size_t)v * V, rv[u]);
+            A::ldv(q + base + (size_t)v * V, qv[u]);
+            const int row = row0 + v / vpr;
+            const int i = row / nt, j = row - i * nt;
+            dv[u] = cf[(size_t)i * P.ntp + j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int v = v0 + u * NT;
+          if (v < nv) {
+            const int k = (v % vpr) * V;
+            typename A::dacc s = A::d_init();
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+              rv[u][e] = A::fma(nalpha, qv[u][e], rv[u][e]);
+              if (k + e < np) A::d_add(s, rv[u][e], rv[u][e]);
+            }
+            A::stvv(r + base + (size_t)v * V, rv[u]);
+            A::d_merge(arr, s);
+            A::d_addw(arho, dv[u], s);
+          }
+        }
+      }
+    } else {
     for (int row = row0 + wy; row < row1; row += NW) {
       const int i = row / nt, j = row - i * nt;
       const coef dinv = cf[(size_t)i * P.ntp + j];
@@ -518,6 +558,7 @@ __global__ void __launch_bounds__(NT, 3)
       // ||r||^2 += s ; rho += Dinv * s
       A::d_merge(arr, s);
       A::d_addw(arho, dinv, s);
+    }
     }
     const double prr = block_sum<NT>(A::d_get(arr), red);
     const double prho = block_sum<NT>(A::d_get(arho), red);

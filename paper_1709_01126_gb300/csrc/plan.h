@@ -6,22 +6,25 @@
 
 #include "kernels.cuh"
 #include "pot3d.h"
+#include "variants.h"
 
 namespace pot3d {
 
 enum { AR_F64 = 0, AR_DF = 1, AR_F32 = 2 };
 
-// Matvec tile shape: TJ theta rows (one warp each) x 32*VK phi columns.
-constexpr int kTJ = 8;
-constexpr int kVK = 2;
-constexpr int kStages8 = 3; // TMA stages for 8-byte elements (FP64, double-float)
-constexpr int kStages4 = 4; // TMA stages for FP32
-constexpr int kUpdThreads = 256;
 constexpr int kAuxThreads = 256;
+constexpr int kRowsPerUpdateItem = 16;
 
 // Per-arithmetic device state of a plan.
 struct ArithData {
-  void *coef = nullptr; // scaled metric table [6][R] in the arithmetic's type
+  // work decomposition: matvec variant, tiles (theta x phi x r-chunks) and
+  // update items (kRowsPerUpdateItem phi rows each)
+  int var = 0;
+  int nJ = 0, nK = 0, ic = 0, nI = 0, tiles_a = 0, rows_b = 0, tiles_b = 0;
+  int cap_a = 0, cap_b = 0; // allocated work-list / partial capacity
+  int2 *d_work_a = nullptr, *d_work_b = nullptr;
+  int *d_nwork = nullptr; // [tiles_a, tiles_b]
+  void *coef = nullptr; // scaled metric table [6][nr][ntp] in the arithmetic's type
   ProbDev *d_prob = nullptr;
   SolveState *d_state = nullptr;
   double *part_a = nullptr, *part_b = nullptr;
@@ -45,10 +48,6 @@ struct Plan {
   // device constant tables
   double *d_c64 = nullptr, *d_S = nullptr, *d_irs = nullptr, *d_its = nullptr, *d_irc = nullptr,
          *d_isd = nullptr, *d_poles = nullptr;
-  // work decomposition
-  int nJ = 0, nK = 0, ic = 0, nI = 0, tiles_a = 0, rows_b = 0, tiles_b = 0;
-  int2 *d_work_a = nullptr, *d_work_b = nullptr;
-  int *d_nwork = nullptr; // [tiles_a, tiles_b] on the device
   ArithData ar[3];
   // workspace (vectors)
   char *ws = nullptr;
@@ -85,7 +84,11 @@ double *ws_r64(const Plan *P);
 int stage(Plan *P, size_t bytes);
 void scaled_table(const Plan *P, std::vector<double> &t);
 int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by);
-int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P);
+int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P, int tj);
+int set_decomposition(Plan *P, int ai, int var, int nI);
+int heuristic_chunks(const Plan *P, const MvVariant &v);
+int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
+                   const Plan *P);
 int default_maxit(const Plan *P);
 
 } // namespace pot3d

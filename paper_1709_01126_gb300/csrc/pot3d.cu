@@ -208,13 +208,13 @@ int ensure_arith(Plan *P, int ai) {
   }
   if (rc) return rc;
   if (cudaMalloc(&A.d_state, sizeof(SolveState)) != cudaSuccess ||
-      cudaMalloc(&A.part_a, sizeof(double) * P->tiles_a) != cudaSuccess ||
-      cudaMalloc(&A.part_b, sizeof(double) * 2 * P->tiles_b) != cudaSuccess ||
       cudaMalloc(&A.d_prob, sizeof(ProbDev)) != cudaSuccess) {
     cudaGetLastError();
     return POT3D_ERR_OOM;
   }
   cudaMemset(A.d_state, 0, sizeof(SolveState));
+  rc = set_decomposition(P, ai, 0, 0);
+  if (rc) return rc;
   A.ready = true;
   return POT3D_OK;
 }
@@ -363,8 +363,18 @@ int pot3d_get_info(const pot3d_plan_t *plan, pot3d_info_t *info) {
   const Plan *P = reinterpret_cast<const Plan *>(plan);
   info->n = (long long)P->n;
   info->pitch = P->pitch;
-  info->tiles_matvec = P->tiles_a;
-  info->tiles_update = P->tiles_b;
+  const int ai = P->prec == POT3D_PREC_FP64 ? AR_F64 : (P->prec == POT3D_PREC_FP64_DF ? AR_DF : AR_F32);
+  if (P->ar[ai].ready) {
+    info->tiles_matvec = P->ar[ai].tiles_a;
+    info->tiles_update = P->ar[ai].tiles_b;
+  } else {
+    int nv = 0;
+    const MvVariant &v = mv_variants(ai, &nv)[0];
+    const int nI = heuristic_chunks(P, v), ic = (P->nr + nI - 1) / nI;
+    info->tiles_matvec = ((P->nt + v.tj - 1) / v.tj) * ((P->np + v.tk - 1) / v.tk) *
+                         ((P->nr + ic - 1) / ic);
+    info->tiles_update = (int)((P->R + kRowsPerUpdateItem - 1) / kRowsPerUpdateItem);
+  }
   info->workspace_bytes = workspace_bytes(P);
   const double es = (P->prec == POT3D_PREC_MIXED) ? 4.0 : 8.0;
   // matvec: read r, p~_old, x~; write p~_new, q, x~.  update: read r, q; write r.

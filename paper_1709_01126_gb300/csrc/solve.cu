@@ -2,7 +2,12 @@
 // and residual entry points.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cudaTypedefs.h>
 
@@ -33,28 +38,6 @@ int plan_device_init(Plan *P) {
   CTRY(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
   CTRY(cudaStreamCreateWithFlags(&P->own_stream, cudaStreamDefault));
   P->stream = P->own_stream;
-  // matvec tiles: theta x phi columns, then enough i-chunks for ~4 waves of
-  // blocks across the SMs without making chunks shorter than 8 planes
-  P->nJ = (P->nt + kTJ - 1) / kTJ;
-  P->nK = (P->np + 32 * kVK - 1) / (32 * kVK);
-  const int cols = P->nJ * P->nK;
-  int nI = (4 * P->nsm + cols - 1) / cols;
-  nI = std::max(1, std::min(nI, std::max(1, P->nr / 8)));
-  P->ic = (P->nr + nI - 1) / nI;
-  P->nI = (P->nr + P->ic - 1) / P->ic;
-  P->tiles_a = cols * P->nI;
-  P->rows_b = 16;
-  P->tiles_b = (int)((P->R + P->rows_b - 1) / P->rows_b);
-  std::vector<int2> wa(P->tiles_a), wb(P->tiles_b);
-  for (int t = 0; t < P->tiles_a; t++) wa[t] = make_int2(0, t);
-  for (int t = 0; t < P->tiles_b; t++) wb[t] = make_int2(0, t);
-  CTRY(cudaMalloc(&P->d_work_a, sizeof(int2) * wa.size()));
-  CTRY(cudaMalloc(&P->d_work_b, sizeof(int2) * wb.size()));
-  CTRY(cudaMemcpy(P->d_work_a, wa.data(), sizeof(int2) * wa.size(), cudaMemcpyHostToDevice));
-  CTRY(cudaMemcpy(P->d_work_b, wb.data(), sizeof(int2) * wb.size(), cudaMemcpyHostToDevice));
-  const int counts[2] = {P->tiles_a, P->tiles_b};
-  CTRY(cudaMalloc(&P->d_nwork, sizeof(counts)));
-  CTRY(cudaMemcpy(P->d_nwork, counts, sizeof(counts), cudaMemcpyHostToDevice));
   auto up = [](double **d, const std::vector<double> &h) -> cudaError_t {
     cudaError_t e = cudaMalloc((void **)d, sizeof(double) * h.size());
     if (e != cudaSuccess) return e;
@@ -87,11 +70,11 @@ void plan_free(Plan *P) {
     cudaFree(A.part_a);
     cudaFree(A.part_b);
     cudaFree(A.d_tma);
+    cudaFree(A.d_work_a);
+    cudaFree(A.d_work_b);
+    cudaFree(A.d_nwork);
   }
   for (auto e : P->ev) cudaEventDestroy(e);
-  cudaFree(P->d_work_a);
-  cudaFree(P->d_work_b);
-  cudaFree(P->d_nwork);
   cudaFree(P->d_c64);
   cudaFree(P->d_S);
   cudaFree(P->d_irs);
@@ -112,29 +95,76 @@ void plan_free(Plan *P) {
 }
 
 // ------------------------------------------------------------- iteration
-template <class A>
-struct MvCfg {
-  static constexpr int S = sizeof(typename A::st) == 8 ? kStages8 : kStages4;
-  using LY = MvLayout<(int)sizeof(typename A::st), kTJ, kVK, S>;
-};
+// r-chunks of a matvec tile column: enough work items for about four waves
+// of blocks across the SMs, chunks no shorter than 8 planes.
+int heuristic_chunks(const Plan *P, const MvVariant &v) {
+  const int nJ = (P->nt + v.tj - 1) / v.tj, nK = (P->np + v.tk - 1) / v.tk;
+  const int cols = nJ * nK;
+  int nI = (4 * P->nsm + cols - 1) / cols;
+  return std::max(1, std::min(nI, std::max(1, P->nr / 8)));
+}
 
-template <class A>
-static int matvec_smem_setup() {
-  static int done = 0;
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, kTJ, kVK, MvCfg<A>::S>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MvCfg<A>::LY::BYTES);
-    if (e != cudaSuccess) return cuda_status(e);
-    done = 1;
+// Sets the matvec variant and r-chunk count of arithmetic ai and uploads
+// the work lists (one problem: items (0, t)).
+int set_decomposition(Plan *P, int ai, int var, int nI) {
+  ArithData &D = P->ar[ai];
+  int nv = 0;
+  const MvVariant *vs = mv_variants(ai, &nv);
+  if (var < 0 || var >= nv) return POT3D_ERR_INVALID_ARG;
+  const MvVariant &v = vs[var];
+  if (nI <= 0) nI = heuristic_chunks(P, v);
+  nI = std::min(nI, P->nr);
+  D.var = var;
+  D.nJ = (P->nt + v.tj - 1) / v.tj;
+  D.nK = (P->np + v.tk - 1) / v.tk;
+  D.ic = (P->nr + nI - 1) / nI;
+  D.nI = (P->nr + D.ic - 1) / D.ic;
+  D.tiles_a = D.nJ * D.nK * D.nI;
+  D.rows_b = kRowsPerUpdateItem;
+  D.tiles_b = (int)((P->R + D.rows_b - 1) / D.rows_b);
+  if (D.tiles_a > D.cap_a) {
+    cudaFree(D.d_work_a);
+    cudaFree(D.part_a);
+    D.d_work_a = nullptr;
+    D.part_a = nullptr;
+    CTRY(cudaMalloc(&D.d_work_a, sizeof(int2) * D.tiles_a));
+    CTRY(cudaMalloc(&D.part_a, sizeof(double) * D.tiles_a));
+    D.cap_a = D.tiles_a;
   }
+  if (D.tiles_b > D.cap_b) {
+    cudaFree(D.d_work_b);
+    cudaFree(D.part_b);
+    D.d_work_b = nullptr;
+    D.part_b = nullptr;
+    CTRY(cudaMalloc(&D.d_work_b, sizeof(int2) * D.tiles_b));
+    CTRY(cudaMalloc(&D.part_b, sizeof(double) * 2 * D.tiles_b));
+    D.cap_b = D.tiles_b;
+  }
+  if (!D.d_nwork) CTRY(cudaMalloc(&D.d_nwork, sizeof(int) * 2));
+  std::vector<int2> wa(D.tiles_a), wb(D.tiles_b);
+  for (int t = 0; t < D.tiles_a; t++) wa[t] = make_int2(0, t);
+  for (int t = 0; t < D.tiles_b; t++) wb[t] = make_int2(0, t);
+  const int counts[2] = {D.tiles_a, D.tiles_b};
+  CTRY(cudaMemcpy(D.d_work_a, wa.data(), sizeof(int2) * wa.size(), cudaMemcpyHostToDevice));
+  CTRY(cudaMemcpy(D.d_work_b, wb.data(), sizeof(int2) * wb.size(), cudaMemcpyHostToDevice));
+  CTRY(cudaMemcpy(D.d_nwork, counts, sizeof(counts), cudaMemcpyHostToDevice));
+  if (v.setup() != 0) return POT3D_ERR_CUDA;
+  // graphs hold the old grid sizes
+  if (D.graph) cudaGraphExecDestroy(D.graph);
+  D.graph = nullptr;
   return POT3D_OK;
 }
 
-template <class A>
 static void launch_matvec(Plan *P, int ai) {
-  k_matvec<A, kTJ, kVK, MvCfg<A>::S><<<P->tiles_a, dim3(32, kTJ), MvCfg<A>::LY::BYTES, P->stream>>>(
-      P->ar[ai].d_prob, P->d_work_a, P->d_nwork);
+  ArithData &D = P->ar[ai];
+  int nv = 0;
+  const MvVariant &v = mv_variants(ai, &nv)[D.var];
+  v.launch(D.d_prob, D.d_work_a, D.d_nwork, D.tiles_a, P->stream);
+}
+
+static void launch_update(Plan *P, int ai) {
+  ArithData &D = P->ar[ai];
+  update_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->stream);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -171,12 +201,12 @@ int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by) 
 }
 
 // metric table [6][nr][ntp]: box of kTJ theta rows x 1 plane x 6 tables
-int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P) {
+int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P, int tj) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return POT3D_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)P->ntp, (cuuint64_t)P->nr, 6u};
   cuuint64_t strides[2] = {(cuuint64_t)P->ntp * es, (cuuint64_t)P->nr * P->ntp * es};
-  cuuint32_t box[3] = {(cuuint32_t)kTJ, 1u, 6u};
+  cuuint32_t box[3] = {(cuuint32_t)tj, 1u, 6u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult cr = fn(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
                    const_cast<void *>(coef), dims, strides, box, estr,
@@ -185,21 +215,27 @@ int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P) {
   return cr == CUDA_SUCCESS ? POT3D_OK : POT3D_ERR_CUDA;
 }
 
-template <class A>
+// TMA descriptors of one problem's vectors for matvec variant v.
+int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
+                   const Plan *P) {
+  const int es = v.es;
+  int rc = encode3d(&T->r, h.r, es, P, v.bw, v.rh);
+  if (!rc) rc = encode3d(&T->p0, h.p0, es, P, v.bw, v.rh);
+  if (!rc) rc = encode3d(&T->p1, h.p1, es, P, v.bw, v.rh);
+  if (!rc) rc = encode3d(&T->x, h.x, es, P, v.tk, v.tj);
+  if (!rc) rc = encode3d(&T->rw, h.r, es, P, v.al, v.rh);
+  if (!rc) rc = encode3d(&T->p0w, h.p0, es, P, v.al, v.rh);
+  if (!rc) rc = encode3d(&T->p1w, h.p1, es, P, v.al, v.rh);
+  if (!rc) rc = encode_coef_map(&T->cf, coef, es, P, v.tj);
+  return rc;
+}
+
 static int build_tma(Plan *P, int ai) {
   ArithData &D = P->ar[ai];
-  using LY = typename MvCfg<A>::LY;
-  constexpr int es = sizeof(typename A::st);
+  int nv = 0;
+  const MvVariant &v = mv_variants(ai, &nv)[D.var];
   ProbDev &h = D.h_prob;
-  TmaSet &T = D.h_tma;
-  int rc = encode3d(&T.r, h.r, es, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.p0, h.p0, es, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.p1, h.p1, es, P, LY::BW, LY::RH);
-  if (!rc) rc = encode3d(&T.x, h.x, es, P, LY::TK, kTJ);
-  if (!rc) rc = encode3d(&T.rw, h.r, es, P, LY::AL, LY::RH);
-  if (!rc) rc = encode3d(&T.p0w, h.p0, es, P, LY::AL, LY::RH);
-  if (!rc) rc = encode3d(&T.p1w, h.p1, es, P, LY::AL, LY::RH);
-  if (!rc) rc = encode_coef_map(&T.cf, D.coef, es, P);
+  int rc = encode_tma_set(&D.h_tma, h, D.coef, v, P);
   if (rc) return rc;
   if (!D.d_tma) {
     if (cudaMalloc(&D.d_tma, sizeof(TmaSet)) != cudaSuccess) {
@@ -208,14 +244,10 @@ static int build_tma(Plan *P, int ai) {
     }
   }
   h.tma = D.d_tma;
-  if (cudaMemcpyAsync(D.d_tma, &T, sizeof(TmaSet), cudaMemcpyHostToDevice, P->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(D.d_tma, &D.h_tma, sizeof(TmaSet), cudaMemcpyHostToDevice, P->stream) !=
+      cudaSuccess)
     return POT3D_ERR_CUDA;
-  return matvec_smem_setup<A>();
-}
-template <class A>
-static void launch_update(Plan *P, int ai) {
-  k_update<A, kUpdThreads><<<P->tiles_b, kUpdThreads, 0, P->stream>>>(P->ar[ai].d_prob,
-                                                                       P->d_work_b, P->d_nwork + 1);
+  return v.setup() == 0 ? POT3D_OK : POT3D_ERR_CUDA;
 }
 
 static int auto_chunk(const Plan *P, int ai) {
@@ -245,9 +277,9 @@ static int iterate(Plan *P, int ai) {
     if (timing) {
       for (int c = 0; c < chunk; c++) {
         CTRY(cudaEventRecord(P->ev[3 * c], P->stream));
-        launch_matvec<A>(P, ai);
+        launch_matvec(P, ai);
         CTRY(cudaEventRecord(P->ev[3 * c + 1], P->stream));
-        launch_update<A>(P, ai);
+        launch_update(P, ai);
         CTRY(cudaEventRecord(P->ev[3 * c + 2], P->stream));
       }
     } else if (graphs) {
@@ -257,8 +289,8 @@ static int iterate(Plan *P, int ai) {
         cudaGraph_t g;
         CTRY(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
         for (int c = 0; c < chunk; c++) {
-          launch_matvec<A>(P, ai);
-          launch_update<A>(P, ai);
+          launch_matvec(P, ai);
+          launch_update(P, ai);
         }
         CTRY(cudaStreamEndCapture(P->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&D.graph, g, 0);
@@ -269,8 +301,8 @@ static int iterate(Plan *P, int ai) {
       CTRY(cudaGraphLaunch(D.graph, P->stream));
     } else {
       for (int c = 0; c < chunk; c++) {
-        launch_matvec<A>(P, ai);
-        launch_update<A>(P, ai);
+        launch_matvec(P, ai);
+        launch_update(P, ai);
       }
     }
     CTRY(cudaGetLastError());
@@ -311,13 +343,13 @@ static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, voi
   h.np = P->np;
   h.pitch = P->pitch;
   h.ntp = P->ntp;
-  h.nJ = P->nJ;
-  h.nK = P->nK;
-  h.ic = P->ic;
-  h.nI = P->nI;
-  h.tiles_a = P->tiles_a;
-  h.rows_b = P->rows_b;
-  h.tiles_b = P->tiles_b;
+  h.nJ = D.nJ;
+  h.nK = D.nK;
+  h.ic = D.ic;
+  h.nI = D.nI;
+  h.tiles_a = D.tiles_a;
+  h.rows_b = D.rows_b;
+  h.tiles_b = D.tiles_b;
   h.plane = (long long)P->nt * P->pitch;
   h.x = x;
   h.r = r;
@@ -393,7 +425,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
        *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
   ArithData &D = P->ar[ai];
   fill_prob<A>(P, ai, x, r, p0, p1, q);
-  TRY(build_tma<A>(P, ai));
+  TRY(build_tma(P, ai));
   cudaStream_t s = P->stream;
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
@@ -456,7 +488,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
        *q = ws_vec(P, 4, 4);
   double *x64 = ws_x64(P), *r64 = ws_r64(P);
   fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q);
-  TRY(build_tma<PF32>(P, AR_F32));
+  TRY(build_tma(P, AR_F32));
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
                        cudaMemcpyDeviceToDevice, s));
@@ -638,3 +670,153 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
 }
 
 } // extern "C"
+
+// ============================================================== autotuner
+namespace pot3d {
+namespace {
+
+struct TuneKey {
+  int nr, nt, np, ai;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(nr, nt, np, ai) < std::tie(o.nr, o.nt, o.np, o.ai);
+  }
+};
+struct TuneVal {
+  int var, nI;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+bool g_tune_loaded = false;
+
+// Optional persistence: POT3D_TUNE_CACHE names a text file of lines
+// "nr nt np arith variant chunks ms".
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("POT3D_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneVal v;
+  while (fscanf(f, "%d %d %d %d %d %d %lf", &k.nr, &k.nt, &k.np, &k.ai, &v.var, &v.nI, &v.ms) == 7)
+    g_tune[k] = v;
+  fclose(f);
+}
+
+void tune_store_locked() {
+  const char *path = getenv("POT3D_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  for (const auto &kv : g_tune)
+    fprintf(f, "%d %d %d %d %d %d %.6f\n", kv.first.nr, kv.first.nt, kv.first.np, kv.first.ai,
+            kv.second.var, kv.second.nI, kv.second.ms);
+  fclose(f);
+}
+
+template <class A>
+int tune_arith(Plan *P, int ai, TuneVal *best) {
+  TRY(ensure_arith(P, ai));
+  TRY(ensure_workspace(P));
+  ArithData &D = P->ar[ai];
+  const size_t es = sizeof(typename A::st);
+  cudaStream_t s = P->stream;
+  CTRY(cudaMemsetAsync(P->ws, 0, 5 * ((P->npad * es + 255) & ~(size_t)255), s));
+  // a running iteration (k > 1, so every TMA box is loaded) on zero vectors
+  SolveState fake{};
+  fake.status = ST_RUNNING;
+  fake.iter = 5;
+  fake.alpha[0] = fake.alpha[1] = 0.5;
+  fake.beta[0] = fake.beta[1] = 0.5;
+  fake.rho = 1.0;
+  fake.bb = 1.0;
+  fake.maxit = 1 << 30;
+  cudaEvent_t e0, e1;
+  CTRY(cudaEventCreate(&e0));
+  CTRY(cudaEventCreate(&e1));
+  int nv = 0;
+  const MvVariant *vs = mv_variants(ai, &nv);
+  best->ms = INFINITY;
+  for (int v = 0; v < nv; v++) {
+    std::vector<int> chunks = {heuristic_chunks(P, vs[v]), 1, 2, 3, 4, 6, 8};
+    std::sort(chunks.begin(), chunks.end());
+    chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
+    for (int nI : chunks) {
+      if (nI > std::max(1, P->nr / 4) && nI != 1) continue;
+      int rc = set_decomposition(P, ai, v, nI);
+      if (rc) return rc;
+      fill_prob<A>(P, ai, ws_vec(P, 0, es), ws_vec(P, 1, es), ws_vec(P, 2, es), ws_vec(P, 3, es),
+                   ws_vec(P, 4, es));
+      TRY(build_tma(P, ai));
+      CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+      float tot = 0.f;
+      const int warm = 2, reps = 5;
+      for (int it = 0; it < warm + reps; it++) {
+        CTRY(cudaMemcpyAsync(D.d_state, &fake, sizeof(fake), cudaMemcpyHostToDevice, s));
+        CTRY(cudaEventRecord(e0, s));
+        launch_matvec(P, ai);
+        CTRY(cudaEventRecord(e1, s));
+        CTRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CTRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (it >= warm) tot += ms;
+      }
+      const double avg = tot / reps;
+      if (avg < best->ms) *best = TuneVal{v, nI, avg};
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return set_decomposition(P, ai, best->var, best->nI);
+}
+
+} // namespace
+} // namespace pot3d
+
+extern "C" int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *chunks,
+                              double *ms) {
+  if (!plan || flags < 0 || flags > 7) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  if (flags == 0)
+    flags = P->prec == POT3D_PREC_FP64 ? 1 : (P->prec == POT3D_PREC_FP64_DF ? 2 : 4);
+  TuneVal last{0, 0, 0.0};
+  for (int ai = 0; ai < 3; ai++) {
+    if (!(flags & (1 << ai))) continue;
+    const TuneKey key{P->nr, P->nt, P->np, ai};
+    TuneVal got{0, 0, 0.0};
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_locked();
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        got = it->second;
+        cached = true;
+      }
+    }
+    int rc;
+    if (cached) {
+      rc = ensure_arith(P, ai);
+      if (!rc) rc = set_decomposition(P, ai, got.var, got.nI);
+    } else if (ai == AR_F64) {
+      rc = tune_arith<PF64>(P, ai, &got);
+    } else if (ai == AR_DF) {
+      rc = tune_arith<PDF>(P, ai, &got);
+    } else {
+      rc = tune_arith<PF32>(P, ai, &got);
+    }
+    if (rc) return fail(rc);
+    if (!cached) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = got;
+      tune_store_locked();
+    }
+    last = got;
+  }
+  if (variant) *variant = last.var;
+  if (chunks) *chunks = last.nI;
+  if (ms) *ms = last.ms;
+  return POT3D_OK;
+}

@@ -65,7 +65,7 @@ class pot3d_info_t(ctypes.Structure):
                 ("bytes_matvec", ctypes.c_double), ("bytes_update", ctypes.c_double)]
 
 
-EXPORTS = ["pot3d_plan", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
+EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
            "pot3d_last_stats", "pot3d_workspace_bytes", "pot3d_set_workspace", "pot3d_solve",
            "pot3d_solve_mixed", "pot3d_field", "pot3d_apply", "pot3d_residual",
            "pot3d_residual_noalloc", "pot3d_batch_create", "pot3d_batch_destroy",
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False):
     L.pot3d_set_opts.argtypes = [P, ctypes.POINTER(pot3d_opts_t)]
     L.pot3d_get_info.argtypes = [P, ctypes.POINTER(pot3d_info_t)]
     L.pot3d_last_stats.argtypes = [P, ctypes.POINTER(pot3d_stats_t)]
+    L.pot3d_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), D]
     L.pot3d_workspace_bytes.argtypes = [P]
     L.pot3d_workspace_bytes.restype = ctypes.c_size_t
     L.pot3d_set_workspace.argtypes = [P, V, ctypes.c_size_t]
@@ -223,6 +224,14 @@ class Plan:
 
     def set_stream(self, stream_handle):
         _check(load().pot3d_set_stream(self.h, stream_handle), "pot3d_set_stream")
+
+    def autotune(self, flags: int = 0):
+        """pot3d_autotune: returns (variant, r-chunks, matvec ms) of the last
+        arithmetic tuned."""
+        v, c, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(load().pot3d_autotune(self.h, int(flags), ctypes.byref(v), ctypes.byref(c),
+                                     ctypes.byref(ms)), "pot3d_autotune")
+        return v.value, c.value, ms.value
 
     def info(self):
         i = pot3d_info_t()

@@ -1,0 +1,101 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (per-kernel event timing on, no graphs).
+
+- 151 x 301 x 601 (the benchmark workload): the first PCG iterates against
+  the oracle's; the full solve to 1e-10 against the stored oracle solve
+  (iteration count +-1, sampled Phi) and its true residual recomputed by the
+  oracle's operator.
+- 401 x 801 x 1601 (514 M unknowns, the largest single-GPU case): the first
+  iterates against the oracle's.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import pot3d_synth as syn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                    "oracle_151x301x601.json")
+C2 = (151, 301, 601)
+
+
+@pytest.fixture(scope="module")
+def p3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_01126_gb300 import pot3d
+
+    pot3d.load(build_if_missing=True)
+    return pot3d
+
+
+@pytest.fixture(scope="module")
+def c2(oracle_mod):
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    br = syn.bipole_br(C2[1], C2[2], seed=1709)
+    g = oracle_mod.Grid(*C2, ratio=1.02)
+    return g, br, g.rhs(br)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-10), ("df", 1e-9)])
+def test_c2_first_iterates(p3, oracle_mod, c2, prec, bound):
+    g, br, b = c2
+    x20, it, st = g.pcg(b, 1e-300, maxit=20)
+    plan = p3.Plan(*C2, ratio=1.02, precision=prec, max_iters=20, time_kernels=1)
+    phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
+    rc, it_gpu = plan.solve(torch.from_numpy(br).cuda(), 1e-300, phi, check=False)
+    assert rc == p3.POT3D_ERR_NOT_CONVERGED and it_gpu == 20
+    assert rel(phi.cpu().numpy(), x20) <= bound
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df", "mixed"])
+def test_c2_full_solve(p3, oracle_mod, c2, prec):
+    g, br, b = c2
+    with open(GOLD) as f:
+        gold = json.load(f)["tol_1e-10"]
+    plan = p3.Plan(*C2, ratio=1.02, precision=prec, time_kernels=1)
+    phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(torch.from_numpy(br).cuda(), 1e-10, phi)
+    x = phi.cpu().numpy()
+    true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    xs = x.ravel()[gold["sample_index"]]
+    ref = np.array(gold["sample_phi"])
+    if prec == "mixed":
+        # refinement stops on the FP64 residual itself
+        assert true_rel <= 1.0001e-10
+        assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-6
+    else:
+        assert abs(it - gold["iters"]) <= 1, (it, gold["iters"])
+        assert true_rel <= (1.05e-10 if prec == "fp64" else 1.5e-10), true_rel
+        assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-9
+    plan.close()
+
+
+def test_c3_first_iterates(p3, oracle_mod):
+    shape = (401, 801, 1601)
+    free, total = torch.cuda.mem_get_info()
+    if free < 30e9:
+        pytest.skip("needs about 25 GB of free device memory")
+    br = syn.bipole_br(shape[1], shape[2], seed=1709)
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    g = oracle_mod.Grid(*shape, ratio=1.02)
+    x5, _, _ = g.pcg(g.rhs(br), 1e-300, maxit=5)
+    brd = torch.from_numpy(br).cuda()
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for prec, bound in (("df", 1e-9), ("fp64", 1e-10)):
+        plan = p3.Plan(*shape, ratio=1.02, precision=prec, max_iters=5, time_kernels=1)
+        rc, it = plan.solve(brd, 1e-300, phi, check=False)
+        assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == 5
+        assert rel(phi.cpu().numpy(), x5) <= bound
+        plan.close()

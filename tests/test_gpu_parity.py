@@ -220,3 +220,25 @@ def test_torch_workspace(p3, oracle_mod):
     phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, it = plan.solve(dev(br), 1e-12, phi)
     assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("prec,flags", [("fp64", 1), ("df", 2), ("mixed", 4)])
+def test_autotune_keeps_parity(p3, oracle_mod, prec, flags):
+    shape, ratio = (14, 37, 150), 1.03
+    br = make_br("bip", 37, 150)
+    g = oracle_mod.Grid(*shape, ratio=ratio)
+    ref, it_ref, _ = g.solve(br, 1e-12)
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec)
+    var, chunks, ms = plan.autotune(flags)
+    assert var >= 0 and chunks >= 1 and ms > 0
+    # a second plan of the same dimensions takes the cached choice
+    plan2 = p3.Plan(*shape, ratio=ratio, precision=prec)
+    assert plan2.autotune(flags)[:2] == (var, chunks)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    if prec == "mixed":
+        plan.solve_mixed(dev(br), 1e-11, phi)
+        b = g.rhs(br)
+        assert np.linalg.norm(b - g.apply(host(phi))) / np.linalg.norm(b) <= 1e-11
+    else:
+        rc, it = plan.solve(dev(br), 1e-12, phi)
+        assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9
