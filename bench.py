@@ -220,6 +220,8 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
     """Times `steps` solves (+ field) of one precision after `warmup` solves."""
     ws, rank, local = dist_env()
     plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=prec, time_kernels=1)
+    # kernel variant and r-chunking chosen by the autotuner (before timing)
+    tuned = plan.autotune(4 if prec == "mixed" else 0)
     info = plan.info()
     phi = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
     B = torch.empty(sum(plan.field_sizes()), dtype=torch.float64, device=dev)
@@ -287,6 +289,7 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
                              "frac_of_measured_hbm": (info["bytes_update"] / (up_ms * 1e-3) / 1e9
                                                       / peaks["hbm_gbs"]) if up_ms else None}
     out = {"value": value, "unit": "iters/s", "ms_per_step": ms_max / steps, "dtype": DTYPES[prec],
+           "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1], "matvec_ms": tuned[2]},
            "iters_per_solve": iters / steps, "hbm_gbs": value / ws * bytes_per_iter / 1e9,
            "bytes_per_iter": bytes_per_iter, "roofline": roof, "gpu_launches": launches,
            "clocks": clk, "steps": steps, "warmup": warmup}
@@ -344,6 +347,7 @@ def run_gpu(args):
                    "parallelism": "replicas x%d" % ws},
         "hbm_gbs": head["hbm_gbs"], "bytes_per_iter": head["bytes_per_iter"],
         "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+        "autotune": head["autotune"],
         "clocks": head["clocks"],
     }
     variants = {}

@@ -206,7 +206,7 @@ void launch_iteration(Batch *B) {
                  vs[v].blocks_per_sm * B->nsm, B->stream);
   }
   update_launcher(AR_F32)(B->d_probs, B->d_work + (size_t)B->n_var * B->work_cap,
-                          B->d_nwork + B->n_var, 3 * B->nsm, B->stream);
+                          B->d_nwork + B->n_var, 2 * B->nsm, B->stream);
 }
 
 // FP64 residual r64 = b - L x64 of slot s and its sums (into d_sums[s][2..3]).

@@ -46,7 +46,14 @@ MvVariant make_variant(int blocks_per_sm) {
 template <class A>
 void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
                cudaStream_t s) {
-  k_update<A, kUpdThreads><<<grid, kUpdThreads, 0, s>>>(probs, work, nwork);
+  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_update<A, kUpdThreads, kUpdSegBytes>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
+    done = true;
+  }
+  k_update<A, kUpdThreads, kUpdSegBytes><<<grid, kUpdThreads, LY::BYTES, s>>>(probs, work, nwork);
 }
 
 } // namespace pot3d

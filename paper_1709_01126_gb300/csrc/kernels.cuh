@@ -455,20 +455,53 @@ __global__ void __launch_bounds__(32 * TJ, 3)
 }
 
 // ------------------------------------------------------------ k_update
-// Work item = (problem, block of rows_b phi rows).  Warps take rows, lanes
-// take 16-byte vectors along phi.  r -= alpha q; per row s = sum r^2, then
-// ||r||^2 += s and rho += D^-1 s.  The last block closes the iteration.
-template <class A, int NT>
-__global__ void __launch_bounds__(NT, 3)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+               " [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared memory of k_update: per warp two stages of (r, q) segments of
+// SEGB bytes each, then two mbarriers per warp.
+template <int NT, int SEGB>
+struct UpLayout {
+  static constexpr int NW = NT / 32;
+  static constexpr int WARP_BYTES = 2 * 2 * SEGB;
+  static constexpr int BYTES = NW * WARP_BYTES + NW * 2 * 8;
+};
+
+// Work item = (problem, block of rows_b phi rows).  Each warp walks its rows
+// (row0 + warp, + NW, ...) in segments of at most SEGB bytes: lane 0 issues
+// cp.async.bulk copies of the r and q segments into the warp's next stage
+// while the warp computes the current one (two stages per warp, completion
+// counted by mbarriers, waits bounded by the global timer).  r -= alpha q is
+// written back from registers; per row s = sum r^2, then ||r||^2 += s and
+// rho += D^-1 s.  The last block closes the iteration.
+template <class A, int NT, int SEGB>
+__global__ void __launch_bounds__(NT)
     k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
              const int *__restrict__ nwork_p) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
-  constexpr int V = A::kVec, NW = NT / 32;
+  using LY = UpLayout<NT, SEGB>;
+  constexpr int V = A::kVec, NW = NT / 32, ES = (int)sizeof(st), SEG = SEGB / ES;
+  static_assert(SEG % (32 * V) == 0, "segment must be whole warp-vectors");
+  extern __shared__ __align__(128) unsigned char smu[];
   __shared__ double red[NW];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, tid = threadIdx.x;
+  st *wbuf = reinterpret_cast<st *>(smu + wy * LY::WARP_BYTES); // [stage][r|q][SEG]
+  uint64_t *wbar = reinterpret_cast<uint64_t *>(smu + NW * LY::WARP_BYTES) + 2 * wy;
+  if (lane == 0) {
+    mbar_init(&wbar[0], 1);
+    mbar_init(&wbar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t useq = 0; // segments this warp consumed so far (stage and parity)
   const int nwork = __ldcg(nwork_p);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 wi = work[w];
@@ -477,88 +510,78 @@ __global__ void __launch_bounds__(NT, 3)
     if (ldcg(&stt->status) != ST_RUNNING) continue;
     const int kit = ldcg(&stt->iter) + 1;
     const int t = wi.y;
-    const int nt = P.nt, np = P.np, pitch = P.pitch;
-    const size_t R = (size_t)P.nr * nt;
-    const int row0 = t * P.rows_b, row1 = min((int)R, row0 + P.rows_b);
+    const int nt = P.nt, np = P.np, pitch = P.pitch, ntp = P.ntp;
+    const long long plane = P.plane;
+    const int R = P.nr * nt;
+    const int row0 = t * P.rows_b, row1 = min(R, row0 + P.rows_b);
     st *__restrict__ r = static_cast<st *>(P.r);
     const st *__restrict__ q = static_cast<const st *>(P.q);
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
     const typename A::scal nalpha = A::scal_from(-ldcg(&stt->alpha[kit & 1]));
-    typename A::dacc arr = A::d_init(), arho = A::d_init();
-    if constexpr (A::kFlatUpdate) {
-      // rows [row0, row1) are contiguous (row-major with pitch): stream them
-      // as one flat run of 16-byte vectors, U per thread in flight, and weight
-      // each vector's sum of squares by its row's Dinv
-      constexpr int U = 4;
-      const int vpr = pitch / V; // vectors per row
-      const int nv = (row1 - row0) * vpr;
-      const size_t base = (size_t)row0 * pitch;
-      for (int v0 = tid; v0 < nv; v0 += NT * U) {
-        val rv[U][V], qv[U][V];
-        coef dv[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int v = v0 + u * NT;
-          if (v < nv) {
-            A::ldv(r + base + (size_t)v * V, rv[u]);
-            A::ldv(q + base + (size_t)v * V, qv[u]);
-            const int row = row0 + v / vpr;
-            const int i = row / nt, j = row - i * nt;
-            dv[u] = cf[(size_t)i * P.ntp + j];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int v = v0 + u * NT;
-          if (v < nv) {
-            const int k = (v % vpr) * V;
-            typename A::dacc s = A::d_init();
-#pragma unroll
-            for (int e = 0; e < V; e++) {
-              rv[u][e] = A::fma(nalpha, qv[u][e], rv[u][e]);
-              if (k + e < np) A::d_add(s, rv[u][e], rv[u][e]);
-            }
-            A::stvv(r + base + (size_t)v * V, rv[u]);
-            A::d_merge(arr, s);
-            A::d_addw(arho, dv[u], s);
-          }
-        }
+    typename A::dacc arr = A::d_init(), arho = A::d_init(), s = A::d_init();
+    const int nseg = (np + SEG - 1) / SEG;
+    const int nrows_w = (row1 - row0 - wy + NW - 1) / NW;
+    const int units = nrows_w > 0 ? nrows_w * nseg : 0;
+    auto unit_row = [&](int u) { return row0 + wy + NW * (u / nseg); };
+    auto unit_off = [&](int u) {
+      const int row = unit_row(u), i = row / nt, j = row - i * nt;
+      return (size_t)i * plane + (size_t)j * pitch + (size_t)(u % nseg) * SEG;
+    };
+    auto unit_len = [&](int u) { return min(SEG, np - (u % nseg) * SEG); };
+    auto issue = [&](int u) {
+      if (lane == 0) {
+        const uint32_t stg = (useq + u) & 1u;
+        const uint32_t bytes = (uint32_t)((unit_len(u) * ES + 15) & ~15);
+        const size_t off = unit_off(u);
+        mbar_expect_tx(&wbar[stg], 2 * bytes);
+        bulk_load(wbuf + (2 * stg) * SEG, r + off, bytes, &wbar[stg]);
+        bulk_load(wbuf + (2 * stg + 1) * SEG, q + off, bytes, &wbar[stg]);
       }
-    } else {
-    for (int row = row0 + wy; row < row1; row += NW) {
-      const int i = row / nt, j = row - i * nt;
-      const coef dinv = cf[(size_t)i * P.ntp + j];
-      const size_t base = (size_t)i * P.plane + (size_t)j * pitch;
-      typename A::dacc s = A::d_init();
-      // U 16-byte vectors of r and of q per lane in flight per step
-      constexpr int U = 4;
-      for (int k = lane * V; k < np; k += 32 * V * U) {
-        val rv[U][V], qv[U][V];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int ku = k + 32 * V * u;
-          if (ku < np) {
-            A::ldv(r + base + ku, rv[u]);
-            A::ldv(q + base + ku, qv[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int ku = k + 32 * V * u;
-          if (ku < np) {
-#pragma unroll
-            for (int e = 0; e < V; e++) {
-              rv[u][e] = A::fma(nalpha, qv[u][e], rv[u][e]);
-              if (ku + e < np) A::d_add(s, rv[u][e], rv[u][e]);
-            }
-            A::stvv(r + base + ku, rv[u]);
-          }
-        }
+    };
+    bool bad = false;
+    if (units > 0) issue(0);
+    int u = 0;
+    for (; u < units; u++) {
+      if (u + 1 < units) issue(u + 1);
+      const uint32_t stg = (useq + u) & 1u;
+      if (!mbar_wait(&wbar[stg], ((useq + u) >> 1) & 1u)) {
+        bad = true;
+        break;
       }
-      // ||r||^2 += s ; rho += Dinv * s
-      A::d_merge(arr, s);
-      A::d_addw(arho, dinv, s);
+      const st *rs = wbuf + (2 * stg) * SEG;
+      const st *qs = wbuf + (2 * stg + 1) * SEG;
+      const int len = unit_len(u);
+      const size_t off = unit_off(u);
+      for (int k = lane * V; k < len; k += 32 * V) {
+        val rv[V], qv[V];
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+          rv[e] = A::ld(rs + k + e);
+          qv[e] = A::ld(qs + k + e);
+        }
+#pragma unroll
+        for (int e = 0; e < V; e++) {
+          rv[e] = A::fma(nalpha, qv[e], rv[e]);
+          if (k + e < len) A::d_add(s, rv[e], rv[e]);
+        }
+        A::stvv(r + off + k, rv);
+      }
+      __syncwarp();
+      if (u % nseg == nseg - 1) {
+        const int row = unit_row(u), i = row / nt, j = row - i * nt;
+        A::d_merge(arr, s);
+        A::d_addw(arho, cf[(size_t)i * ntp + j], s);
+        s = A::d_init();
+      }
     }
+    if (bad) {
+      // drain this warp's copy still in flight (bounded), then report
+      if (u + 1 < units) mbar_wait(&wbar[(useq + u + 1) & 1u], ((useq + u + 1) >> 1) & 1u);
+    }
+    useq += units;
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) stt->status = ST_TIMEOUT;
+      break;
     }
     const double prr = block_sum<NT>(A::d_get(arr), red);
     const double prho = block_sum<NT>(A::d_get(arho), red);

@@ -13,7 +13,7 @@ namespace pot3d {
 enum { AR_F64 = 0, AR_DF = 1, AR_F32 = 2 };
 
 constexpr int kAuxThreads = 256;
-constexpr int kRowsPerUpdateItem = 16;
+constexpr int kRowsPerUpdateItem = 32;
 
 // Per-arithmetic device state of a plan.
 struct ArithData {

@@ -28,5 +28,6 @@ const MvVariant *mv_variants(int ai, int *count);
 KLaunch update_launcher(int ai);
 
 constexpr int kUpdThreads = 256;
+constexpr int kUpdSegBytes = 2560; // bytes of r (and of q) per warp stage
 
 } // namespace pot3d

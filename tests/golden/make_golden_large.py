@@ -27,12 +27,16 @@ def make():
     out = {"shape": list(shape), "ratio": ratio, "br": "bipole_br(seed=1709, 200 bipoles)"}
     for tol in (1e-10,):
         t = time.time()
-        x, it, st = g.pcg(b, tol)
+        x, it, st, hist = g.pcg(b, tol, history=True)
         idx = np.random.default_rng(1).integers(0, g.n, 64)
+        tail0 = max(0, it - 40)
         out["tol_%g" % tol] = {"iters": it, "status": st, "seconds": time.time() - t,
                                "sample_index": idx.tolist(),
                                "sample_phi": [float(v) for v in x.ravel()[idx]],
-                               "phi_norm2": float(np.linalg.norm(x))}
+                               "phi_norm2": float(np.linalg.norm(x)),
+                               "relres_tail_start": tail0,
+                               "relres_tail": [float(v) for v in hist[tail0:]],
+                               "threads": oracle.get_threads()}
     return out
 
 
