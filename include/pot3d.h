@@ -97,8 +97,16 @@ typedef struct {
   int chunk;          /* iterations enqueued between host polls; 0: automatic        */
   int use_graphs;     /* 0: automatic (graphs on), 1: on, -1: off                    */
   int time_kernels;   /* 1: time every iteration kernel with CUDA events (no graphs) */
-  double inner_tol;   /* MIXED: relative tolerance of each inner FP32 solve (0: 1e-4) */
-  int max_outer;      /* MIXED: refinement cap (0: 30)                               */
+  double inner_tol;   /* MIXED: the inner FP32 PCG hands over to an FP64 refinement
+                         step once its residual fell by this factor (0: 0.1 with
+                         mixed_restart = 0, 1e-4 with mixed_restart = 1)         */
+  int max_outer;      /* MIXED: refinement cap (0: 30 restarts, 200 replacements)    */
+  int mixed_restart;  /* MIXED: 0 = after each FP64 step the inner PCG continues on
+                         the replaced residual with its search direction kept
+                         (reliable updates; a segment that needs more than
+                         20*(nr+nt+np) iterations ends and the next one
+                         restarts); 1 = it always restarts from zero (plain
+                         defect correction)                                      */
 } pot3d_opts_t;
 
 /* Statistics of the last solve on a plan. */

@@ -91,6 +91,29 @@ static __global__ void k_start(SolveState *st, const double *sums, double n0, do
   st->status = (relres <= tol) ? ST_CONVERGED : ST_RUNNING;
 }
 
+// Residual replacement of the refinement loop (reliable update): the inner
+// PCG stopped after iteration K; its correction was folded into x64, the
+// FP64 residual recomputed and scaled into r32 (sums: ||r32||^2 and
+// sum Dinv r32^2).  The iteration continues from K with the search
+// direction kept: the x~ term of iteration K is void (alpha_K = 0, x~ = 0)
+// and beta_K = rho_new / rho_{K-1} * (s_old / s_new) absorbs the change of
+// scale of p~.
+static __global__ void k_resume(SolveState *st, const double *sums, double ratio, double tol,
+                                int seg_cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int K = st->iter;
+  st->maxit = K + seg_cap; // a segment that stalls ends on the cap and restarts
+  const double bb = sums[0], rho = sums[1];
+  st->alpha[K & 1] = 0.0;
+  st->beta[K & 1] = rho / st->rho * ratio;
+  st->rho = rho;
+  st->bb = bb;
+  st->tol = tol;
+  st->relres = 1.0;
+  st->ticket_a = st->ticket_b = 0u;
+  st->status = (bb > 0.0 && isfinite(bb)) ? ST_RUNNING : ST_CONVERGED;
+}
+
 // r (plane 0, padded) = scale * b.
 template <class A>
 __global__ void k_write_rhs(const double *__restrict__ br, const double *__restrict__ S, int nt,

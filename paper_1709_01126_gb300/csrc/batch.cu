@@ -85,7 +85,8 @@ struct Slot {
   size_t off = 0, bytes = 0;
   float *v32[5] = {}; // x~, r, p~0, p~1, q
   double *x64 = nullptr, *r64 = nullptr, *part_a = nullptr, *part_b = nullptr, *part_aux = nullptr;
-  int outer = 0, inner = 0, status = POT3D_OK;
+  int outer = 0, inner = 0, status = POT3D_OK, iter0 = 0;
+  bool resumable = false; // the inner PCG stopped cleanly and may continue
   double relres = INFINITY, prev = INFINITY, scale = 1.0;
 };
 
@@ -219,24 +220,35 @@ void launch_outer_residual(Batch *B, int s) {
   k_sum_pairs<kBThreads><<<1, kBThreads, 0, B->stream>>>(S.part_aux, g, B->d_sums + 4 * s + 2);
 }
 
-// Starts the inner FP32 solve of slot s on scale * r64.
-void launch_inner_start(Batch *B, int s) {
+// Starts (or, after a clean stop, resumes with the search direction kept)
+// the inner FP32 solve of slot s on new_scale * r64.
+void launch_inner_start(Batch *B, int s, double new_scale) {
   Slot &S = B->slots[s];
   Plan *P = S.plan;
   const int g = grid_for(B, P->n);
   const float *dinv32 = static_cast<const float *>(P->ar[AR_F32].coef);
   k_inner_rhs<kBThreads><<<g, kBThreads, 0, B->stream>>>(S.r64, dinv32, P->nr, P->nt, P->ntp, P->np,
-                                                         P->pitch, S.scale, S.v32[1], S.part_aux);
+                                                         P->pitch, new_scale, S.v32[1], S.part_aux);
   k_sum_pairs<kBThreads><<<1, kBThreads, 0, B->stream>>>(S.part_aux, g, B->d_isums + 2 * s);
   const size_t v4 = al(P->npad * 4);
+  const bool restart = B->opts.mixed_restart != 0;
+  const double inner_tol =
+      B->opts.inner_tol > 0 ? B->opts.inner_tol : (restart ? 1e-4 : 0.1);
   cudaMemsetAsync(S.v32[0], 0, v4, B->stream);
-  cudaMemsetAsync(S.v32[2], 0, v4, B->stream);
-  cudaMemsetAsync(S.v32[3], 0, v4, B->stream);
-  cudaMemsetAsync(S.v32[4], 0, v4, B->stream);
-  const double inner_tol = B->opts.inner_tol > 0 ? B->opts.inner_tol : 1e-4;
-  const int maxit = B->opts.max_iters > 0 ? B->opts.max_iters : default_maxit(P);
-  k_start<<<1, 1, 0, B->stream>>>(B->d_states + s, B->d_isums + 2 * s, (double)P->n, inner_tol,
-                                  maxit, 0, 1.0);
+  if (S.resumable && !restart) {
+    S.iter0 = B->h_states[s].iter;
+    k_resume<<<1, 1, 0, B->stream>>>(B->d_states + s, B->d_isums + 2 * s, S.scale / new_scale,
+                                     inner_tol, segment_cap(P));
+  } else {
+    S.iter0 = 0;
+    cudaMemsetAsync(S.v32[2], 0, v4, B->stream);
+    cudaMemsetAsync(S.v32[3], 0, v4, B->stream);
+    cudaMemsetAsync(S.v32[4], 0, v4, B->stream);
+    const int maxit = B->opts.max_iters > 0 ? B->opts.max_iters : default_maxit(P);
+    k_start<<<1, 1, 0, B->stream>>>(B->d_states + s, B->d_isums + 2 * s, (double)P->n, inner_tol,
+                                    maxit, 0, 1.0);
+  }
+  S.scale = new_scale;
 }
 
 void release_slot(Batch *B, int s) {
@@ -256,8 +268,9 @@ int advance_outer(Batch *B, bool starting_only) {
       todo.push_back(s);
     } else if (!starting_only && S.phase == PH_INNER && B->h_states[s].status != ST_RUNNING) {
       const SolveState &hs = B->h_states[s];
-      S.inner += hs.iter;
-      if (hs.status == ST_BREAKDOWN && hs.iter == 0) {
+      S.inner += hs.iter - S.iter0;
+      S.resumable = (hs.status == ST_CONVERGED);
+      if (hs.status == ST_BREAKDOWN && hs.iter == S.iter0) {
         S.status = POT3D_ERR_BREAKDOWN;
         S.phase = PH_DONE;
         continue;
@@ -275,7 +288,8 @@ int advance_outer(Batch *B, bool starting_only) {
                       cudaMemcpyDeviceToHost, B->stream) != cudaSuccess ||
       cudaStreamSynchronize(B->stream) != cudaSuccess)
     return POT3D_ERR_CUDA;
-  const int max_outer = B->opts.max_outer > 0 ? B->opts.max_outer : 30;
+  const bool restart = B->opts.mixed_restart != 0;
+  const int max_outer = B->opts.max_outer > 0 ? B->opts.max_outer : (restart ? 30 : 200);
   for (int s : todo) {
     Slot &S = B->slots[s];
     const double bb = B->h_sums[4 * s], rr = B->h_sums[4 * s + 2];
@@ -288,7 +302,7 @@ int advance_outer(Batch *B, bool starting_only) {
     } else if (relres <= S.tol) {
       S.status = POT3D_OK;
       done = true;
-    } else if (S.outer >= max_outer || !(relres < 0.5 * S.prev)) {
+    } else if (S.outer >= max_outer || !(relres < (restart ? 0.5 : 1.0) * S.prev)) {
       S.status = POT3D_ERR_NOT_CONVERGED;
       done = true;
     }
@@ -302,8 +316,7 @@ int advance_outer(Batch *B, bool starting_only) {
       continue;
     }
     S.prev = relres;
-    S.scale = std::ldexp(1.0, -std::ilogb(std::sqrt(rr / (double)S.plan->n)));
-    launch_inner_start(B, s);
+    launch_inner_start(B, s, std::ldexp(1.0, -std::ilogb(std::sqrt(rr / (double)S.plan->n))));
     S.phase = PH_INNER;
   }
   if (cudaGetLastError() != cudaSuccess) return POT3D_ERR_CUDA;

@@ -90,5 +90,6 @@ int heuristic_chunks(const Plan *P, const MvVariant &v);
 int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
                    const Plan *P);
 int default_maxit(const Plan *P);
+int segment_cap(const Plan *P);
 
 } // namespace pot3d

@@ -260,7 +260,7 @@ static int auto_chunk(const Plan *P, int ai) {
 }
 
 template <class A>
-static int iterate(Plan *P, int ai) {
+static int iterate(Plan *P, int ai, int iter0 = 0) {
   ArithData &D = P->ar[ai];
   const bool timing = P->opts.time_kernels != 0;
   const bool graphs = !timing && P->opts.use_graphs >= 0;
@@ -272,7 +272,7 @@ static int iterate(Plan *P, int ai) {
       P->ev.push_back(e);
     }
   }
-  int done_before = 0, last_iter = -1;
+  int done_before = iter0, last_iter = iter0 - 1;
   for (;;) {
     if (timing) {
       for (int c = 0; c < chunk; c++) {
@@ -373,6 +373,10 @@ static int status_code(int st) {
 }
 
 int default_maxit(const Plan *P) { return 100 * (P->nr + P->nt + P->np); }
+
+// Iterations one continued inner segment may take before it is ended and
+// the next refinement step restarts the inner PCG from zero.
+int segment_cap(const Plan *P) { return 20 * (P->nr + P->nt + P->np); }
 
 // Inputs may be host or device pointers; host arrays are staged through
 // one device buffer [br | phi | B].
@@ -506,13 +510,16 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
   const int gn = aux_grid(P, P->n);
   const float *dinv32 = static_cast<const float *>(D.coef); // slab 0 of the F32 table
-  const double inner_tol = P->opts.inner_tol > 0 ? P->opts.inner_tol : 1e-4;
-  const int max_outer = P->opts.max_outer > 0 ? P->opts.max_outer : 30;
+  const bool restart = P->opts.mixed_restart != 0;
+  const double inner_tol =
+      P->opts.inner_tol > 0 ? P->opts.inner_tol : (restart ? 1e-4 : 0.1);
+  const int max_outer = P->opts.max_outer > 0 ? P->opts.max_outer : (restart ? 30 : 200);
   const int inner_maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
   memset(&P->stats, 0, sizeof(P->stats));
   P->stats.launches = 2 + (x0 ? 1 : 0);
   int n_outer = 0, n_inner = 0, status = POT3D_OK;
-  double bb = 0.0, prev = INFINITY, relres = INFINITY;
+  double bb = 0.0, prev = INFINITY, relres = INFINITY, scale = 1.0;
+  bool resumable = false; // an inner PCG stopped cleanly and may continue
   for (;;) {
     k_op64<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.br, P->d_S, P->d_c64, P->nr,
                                                    P->nt, P->np, 0, r64, P->pitch, P->d_part);
@@ -529,32 +536,45 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
       break;
     }
     if (relres <= tol) break;
-    if (n_outer >= max_outer || !(relres < 0.5 * prev)) {
+    // restarts must gain a factor 2 per step; replacements only must not
+    // grow the residual
+    if (n_outer >= max_outer || !(relres < (restart ? 0.5 : 1.0) * prev)) {
       status = POT3D_ERR_NOT_CONVERGED;
       break;
     }
     prev = relres;
     // inner system L d = scale * r64 in FP32
     const double rms = std::sqrt(rr / (double)P->n);
-    const double scale = std::ldexp(1.0, -std::ilogb(rms));
+    const double new_scale = std::ldexp(1.0, -std::ilogb(rms));
     k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->ntp, P->np,
-                                                        P->pitch, scale, (float *)r, P->d_part);
+                                                        P->pitch, new_scale, (float *)r, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 4);
     CTRY(cudaMemsetAsync(x, 0, v4, s));
-    CTRY(cudaMemsetAsync(p0, 0, v4, s));
-    CTRY(cudaMemsetAsync(p1, 0, v4, s));
-    CTRY(cudaMemsetAsync(q, 0, v4, s));
-    k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, (double)P->n, inner_tol, inner_maxit, 0,
-                            1.0);
-    P->stats.launches += 4;
+    int iter0 = 0;
+    if (resumable && !restart) {
+      // reliable update: keep p~ and the iteration count
+      k_resume<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, scale / new_scale, inner_tol,
+                               segment_cap(P));
+      iter0 = P->h_state->iter;
+      P->stats.launches += 3;
+    } else {
+      CTRY(cudaMemsetAsync(p0, 0, v4, s));
+      CTRY(cudaMemsetAsync(p1, 0, v4, s));
+      CTRY(cudaMemsetAsync(q, 0, v4, s));
+      k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, (double)P->n, inner_tol, inner_maxit, 0,
+                              1.0);
+      P->stats.launches += 4;
+    }
+    scale = new_scale;
     CTRY(cudaGetLastError());
-    TRY(iterate<PF32>(P, AR_F32));
+    TRY(iterate<PF32>(P, AR_F32, iter0));
     const SolveState &hs = *P->h_state;
-    n_inner += hs.iter;
-    if (hs.status == ST_BREAKDOWN && hs.iter == 0) {
+    n_inner += hs.iter - iter0;
+    if (hs.status == ST_BREAKDOWN && hs.iter == iter0) {
       status = POT3D_ERR_BREAKDOWN;
       break;
     }
+    resumable = (hs.status == ST_CONVERGED);
     k_refine_update<<<gn, kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, x64, 1.0 / scale);
     P->stats.launches += 1;
     n_outer++;

@@ -50,7 +50,8 @@ class pot3d_bc_t(ctypes.Structure):
 class pot3d_opts_t(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("use_x0", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("mixed_restart", ctypes.c_int)]
 
 
 class pot3d_stats_t(ctypes.Structure):
@@ -217,9 +218,9 @@ class Plan:
             pass
 
     def set_opts(self, max_iters=0, use_x0=0, chunk=0, use_graphs=0, time_kernels=0,
-                 inner_tol=0.0, max_outer=0):
+                 inner_tol=0.0, max_outer=0, mixed_restart=0):
         o = pot3d_opts_t(int(max_iters), int(use_x0), int(chunk), int(use_graphs), int(time_kernels),
-                         float(inner_tol), int(max_outer))
+                         float(inner_tol), int(max_outer), int(mixed_restart))
         _check(load().pot3d_set_opts(self.h, ctypes.byref(o)), "pot3d_set_opts")
 
     def set_stream(self, stream_handle):
@@ -302,14 +303,15 @@ class Batch:
     """Owns a pot3d_batch_t (continuous batching of mixed-precision solves)."""
 
     def __init__(self, max_bytes: int, max_slots: int = 256, inner_tol=0.0, max_outer=0,
-                 max_iters=0):
+                 max_iters=0, mixed_restart=0):
         L = load()
         h = L.pot3d_batch_create(int(max_bytes), int(max_slots))
         if not h:
             raise Pot3dError(L.pot3d_last_error(), "pot3d_batch_create")
         self.h = h
         self.max_slots = int(max_slots)
-        o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer))
+        o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer),
+                         int(mixed_restart))
         _check(L.pot3d_batch_set_opts(h, ctypes.byref(o)), "pot3d_batch_set_opts")
 
     def close(self):
