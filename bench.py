@@ -144,6 +144,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+# captures summarised in profiles/k_matvec_k_update_151x301x601.md (same
+# kernels and tuned configuration as timed here)
+TRAFFIC = {"fp64": 1.2807e9, "df": 1.2789e9, "mixed": 0.6187e9}
+
 # FP64 FMA units: 152 SMs x 2 per clock at the 2070 MHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 FMAs per point of the matvec kernel (p~ and x~ updates, 6-term
@@ -272,7 +277,7 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
         achieved = 2 * FP64_FMA_PER_POINT_MATVEC * n / (mv_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_matvec<PF64>", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
+                "traffic": TRAFFIC.get(prec),
                 "peak_source": "FP64 FMA units x max SM clock: 152 x 2/clk x 2 flop x 2.07 GHz",
                 "hbm_GB_s": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9,
                 "hbm_frac_of_measured": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
@@ -280,7 +285,7 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
         achieved = info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "k_matvec<%s>" % ("PDF" if prec == "df" else "PF32"),
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC.get(prec),
                 "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % src}
     roof["avg_launch_ms"] = mv_ms
     roof["algorithmic_bytes_per_launch"] = info["bytes_matvec"]
