@@ -391,6 +391,10 @@ def run_serve(args):
     batched = serve.run_batched(reqs, inputs, batch_bytes=budget, k=args.batch_k,
                                 inner_tol=args.inner_tol)
     base = serve.run_fp64_serial(reqs, inputs)
+    # capacity: the same requests all present at t = 0
+    sat_reqs = [serve.Request(r.rid, r.grid, 0.0, r.seed) for r in reqs]
+    sat = serve.run_batched(sat_reqs, inputs, batch_bytes=budget, k=args.batch_k,
+                            inner_tol=args.inner_tol).summary()
     b, f = batched.summary(), base.summary()
     line = {"metric": METRIC, "value": b["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.requests, "warmup": 0, "higher_is_better": True, "scaling": "weak",
@@ -401,6 +405,9 @@ def run_serve(args):
                        "batch_arena_bytes": budget, "step_iters": args.batch_k},
             "batched": b, "fp64_one_at_a_time": f,
             "speedup_solves_per_s": b["solves_per_s"] / f["solves_per_s"],
+            "capacity_solves_per_s": {"batched_all_at_t0": sat["solves_per_s"],
+                                      "fp64_one_at_a_time": rate64,
+                                      "ratio": sat["solves_per_s"] / rate64},
             "fp64_calibration_s": dict(zip(["x".join(map(str, g)) for g in serve.GRIDS], times))}
     print(json.dumps(line), flush=True)
     return 0
