@@ -413,6 +413,59 @@ def run_serve(args):
     return 0
 
 
+def run_large(args):
+    """The largest single-GPU case, 401 x 801 x 1601 (514 M unknowns, same
+    stretching and Br generator): PCG iterations/s over a fixed number of
+    iterations per step (the full solve needs far more iterations than a
+    benchmark run can afford), FP64 and double-float."""
+    import torch
+
+    from paper_1709_01126_gb300 import pot3d
+    import pot3d_synth as syn
+
+    pot3d.load()
+    shape = (401, 801, 1601)
+    br_d = torch.from_numpy(syn.bipole_br(shape[1], shape[2], seed=SEED)).cuda()
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    n = shape[0] * shape[1] * shape[2]
+    out = {}
+    peaks, src = measured_peaks()
+    for prec in ("fp64", "df"):
+        plan = pot3d.Plan(*shape, ratio=RATIO, precision=prec, max_iters=args.large_iters,
+                          time_kernels=1)
+        tuned = plan.autotune(0)
+        plan.solve(br_d, 1e-300, phi, check=False)  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iters = 0
+        for _ in range(args.steps):
+            rc, it = plan.solve(br_d, 1e-300, phi, check=False)
+            iters += it
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        st = plan.stats()
+        info = plan.info()
+        mv = st["kernel_ms"][0] / max(st["kernel_ms"][2], 1)
+        up = st["kernel_ms"][1] / max(st["kernel_ms"][3], 1)
+        out[prec] = {"iters_per_s": iters / dt, "matvec_ms": mv, "update_ms": up,
+                     "matvec_GB_s": info["bytes_matvec"] / (mv * 1e-3) / 1e9,
+                     "update_GB_s": info["bytes_update"] / (up * 1e-3) / 1e9,
+                     "hbm_GB_s_per_iter_model": 72.0 * n * iters / dt / 1e9,
+                     "workspace_GB": info["workspace_bytes"] / 1e9,
+                     "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1]}}
+        plan.close()
+    line = {"metric": METRIC, "value": out["fp64"]["iters_per_s"], "unit": "iters/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "workload_kind": "large",
+            "config": {"workload": "401x801x1601 (514M unknowns), r geometric 1.02, 200 bipoles, "
+                                   "%d PCG iterations per step" % args.large_iters,
+                       "hbm_peak_GB_s": peaks["hbm_gbs"]},
+            "fp64": out["fp64"], "df": out["df"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Short solve for ncu: the same 151x301x601 problem, capped at a few
     PCG iterations so a capture ends quickly."""
@@ -450,7 +503,8 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
-    ap.add_argument("--workload", default="pcg", choices=["pcg", "serve"])
+    ap.add_argument("--workload", default="pcg", choices=["pcg", "serve", "large"])
+    ap.add_argument("--large-iters", type=int, default=200)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--batch-k", type=int, default=16)
     ap.add_argument("--inner-tol", type=float, default=0.0)
@@ -464,6 +518,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_gpu(args)
 
 

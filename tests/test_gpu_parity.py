@@ -242,3 +242,45 @@ def test_autotune_keeps_parity(p3, oracle_mod, prec, flags):
     else:
         rc, it = plan.solve(dev(br), 1e-12, phi)
         assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df", "mixed"])
+def test_gpu_closed_form_second_order(p3, prec):
+    """The GPU solution itself converges to the analytic shell potential of
+    Br = Y_3^2 at second order (Sec. 2.2), independently of the oracle."""
+    l, m, R1 = 3, 2, 2.5
+    M = np.array([[l, -(l + 1.0)], [R1 ** l, R1 ** (-(l + 1.0))]])
+    a, b = np.linalg.solve(M, np.array([1.0, 0.0]))
+    errs = []
+    for n in (10, 20, 40):
+        shape = (n, n, 2 * n)
+        br, scale = syn.ylm_br(n, 2 * n, l, m)
+        plan = p3.Plan(*shape, ratio=1.0, precision=prec)
+        phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        plan.solve(dev(br), 1e-12, phi)
+        rc = (np.arange(n) + 0.5) * (1.5 / n) + 1.0
+        tc = (np.arange(n) + 0.5) * (np.pi / n)
+        pc = (np.arange(2 * n) + 0.5) * (2 * np.pi / (2 * n))
+        R, T, P = np.meshgrid(rc, tc, pc, indexing="ij")
+        ex = (a * R ** l + b * R ** (-(l + 1.0))) * syn.ylm_shape(l, m, T, P, scale)
+        errs.append(rel(host(phi), ex))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.9), (errs, orders)
+
+
+def test_explicit_faces_match_oracle(p3, oracle_mod):
+    """Explicit nonuniform r and theta faces (Sec. 2.2: nonuniform in r and
+    theta) give the oracle's solution."""
+    nr, nt, np_ = 11, 17, 40
+    rf = 1.0 + 1.5 * (np.linspace(0, 1, nr + 1) ** 1.3)
+    u = np.linspace(0, 1, nt + 1)
+    tf = np.pi * (u + 0.12 * np.sin(2 * np.pi * u) / (2 * np.pi))
+    tf[0], tf[-1] = 0.0, np.pi
+    br = make_br("bip", nt, np_)
+    g = oracle_mod.Grid(nr, nt, np_, r_faces=rf, t_faces=tf)
+    ref, it_ref, _ = g.solve(br, 1e-12)
+    for prec in ("fp64", "df"):
+        plan = p3.Plan(nr, nt, np_, r_faces=rf, t_faces=tf, precision=prec)
+        phi = torch.zeros((nr, nt, np_), dtype=torch.float64, device="cuda")
+        rc, it = plan.solve(dev(br), 1e-12, phi)
+        assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9
