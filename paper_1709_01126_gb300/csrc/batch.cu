@@ -117,6 +117,7 @@ struct pot3d_batch {
   int *d_nwork = nullptr; // [n_var + 1]
   int work_cap = 0;
   unsigned var_mask = 0, graph_mask = 0; // variants with work now / in the graph
+  int cap_of[8] = {};                    // grid of each list in the captured graph
   bool dirty = true;
   cudaStream_t stream = nullptr, own_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -192,22 +193,32 @@ int rebuild_work(Batch *B) {
   // the host vectors above are pageable and local: finish the copies here
   if (cudaStreamSynchronize(B->stream) != cudaSuccess) return POT3D_ERR_CUDA;
   B->var_mask = mask;
+  // a captured graph launches cap_of[v] blocks per list: grow (and
+  // re-capture) when a list outgrows it, in steps to limit re-captures
+  for (int v = 0; v < nl; v++) {
+    if (counts[v] > B->cap_of[v]) {
+      B->cap_of[v] = std::max(counts[v], 2 * B->cap_of[v]);
+      if (B->graph) cudaGraphExecDestroy(B->graph);
+      B->graph = nullptr;
+    }
+  }
   B->dirty = false;
   return POT3D_OK;
 }
 
 // One iteration of every running slot: the matvec of each variant present,
-// then the update, all persistent (a few blocks per SM looping over items).
+// then the update.  Grids cover the work lists' capacity (the lists and their
+// lengths are read from device memory; blocks past the length exit at once).
 void launch_iteration(Batch *B) {
   int nv = 0;
   const MvVariant *vs = mv_variants(AR_F32, &nv);
   for (int v = 0; v < B->n_var; v++) {
     if (!(B->graph_mask & (1u << v))) continue;
     vs[v].launch(B->d_probs, B->d_work + (size_t)v * B->work_cap, B->d_nwork + v,
-                 vs[v].blocks_per_sm * B->nsm, B->stream);
+                 std::max(1, B->cap_of[v]), B->stream);
   }
   update_launcher(AR_F32)(B->d_probs, B->d_work + (size_t)B->n_var * B->work_cap,
-                          B->d_nwork + B->n_var, 2 * B->nsm, B->stream);
+                          B->d_nwork + B->n_var, std::max(1, B->cap_of[B->n_var]), B->stream);
 }
 
 // FP64 residual r64 = b - L x64 of slot s and its sums (into d_sums[s][2..3]).

@@ -159,6 +159,8 @@ static void launch_matvec(Plan *P, int ai) {
   ArithData &D = P->ar[ai];
   int nv = 0;
   const MvVariant &v = mv_variants(ai, &nv)[D.var];
+  // one block per tile: the hardware block scheduler balances tiles of
+  // unequal cost better than a persistent grid (measured)
   v.launch(D.d_prob, D.d_work_a, D.d_nwork, D.tiles_a, P->stream);
 }
 
