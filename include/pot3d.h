@@ -145,10 +145,11 @@ int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *opts);
 int pot3d_get_info(const pot3d_plan_t *plan, pot3d_info_t *info);
 int pot3d_last_stats(const pot3d_plan_t *plan, pot3d_stats_t *stats);
 
-/* Autotuner: times every matvec tile-shape variant and r-chunk count of the
- * selected arithmetics on this plan's problem (a few launches each, on the
- * plan's stream, with the plan's workspace) and keeps the fastest for later
- * solves.  flags: bit 0 FP64, bit 1 double-float, bit 2 FP32 (the inner
+/* Autotuner: times every matvec tile-shape variant and r-chunk count, then
+ * the update kernel's rows per work item (16, 32, 64, 128), of the selected
+ * arithmetics on this plan's problem (a few launches each, on the plan's
+ * stream, with the plan's workspace) and keeps the fastest for later
+ * solves (pot3d_get_info reports the resulting work-item counts).  flags: bit 0 FP64, bit 1 double-float, bit 2 FP32 (the inner
  * solve of refinement and batches); 0 = the plan's own precision.  Results
  * are cached per (nr, nt, np, arithmetic) for the process and, when the
  * environment names a file in POT3D_TUNE_CACHE, across processes.

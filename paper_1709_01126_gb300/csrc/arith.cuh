@@ -108,9 +108,14 @@ __device__ __forceinline__ void cacc_add_prodf(cacc &A, float a, float b) {
   float e = __fmaf_rn(a, b, -p);
   cacc_add(A, p, e);
 }
+// Renormalise to a double-float.  s is the rounded running sum and c the
+// accumulated rounding errors, so |c| <= |s| except when the sum cancels to
+// below the accumulation's own error bound (about n^2 2^-48 of the sum of
+// |terms|); FastTwoSum is exact in the first case and in the second adds
+// an error of the order of ulp(c), inside that same bound.
 __device__ __forceinline__ dfl cacc_get(cacc A) {
   dfl z;
-  two_sum(A.s, A.c, z.h, z.l);
+  fast_two_sum(A.s, A.c, z.h, z.l);
   return z;
 }
 
@@ -173,8 +178,21 @@ struct PDF {
   static __device__ __forceinline__ void stv(st *p, val v) { *p = make_float2(v.h, v.l); }
   static __device__ __forceinline__ val zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ scal scal_from(double x) { return df_from_double(x); }
+  // y + a x: the product's leading part exactly (TwoProd) plus its cross
+  // terms, added to y with one TwoSum and a final FastTwoSum (the product
+  // is not renormalised on its own; same error order as SloppyDWPlusDW of
+  // DWTimesDW, four operations fewer)
   static __device__ __forceinline__ val fma(scal a, val x, val y) {
-    return df_add_sloppy(y, df_mul(a, x));
+    const float ph = __fmul_rn(a.h, x.h);
+    float pl = __fmaf_rn(a.h, x.h, -ph);
+    pl = __fmaf_rn(a.h, x.l, pl);
+    pl = __fmaf_rn(a.l, x.h, pl);
+    float sh, sl;
+    two_sum(y.h, ph, sh, sl);
+    sl = __fadd_rn(sl, __fadd_rn(y.l, pl));
+    dfl z;
+    fast_two_sum(sh, sl, z.h, z.l);
+    return z;
   }
   static __device__ __forceinline__ sacc s_init(val c) { return {c.h, c.l}; }
   static __device__ __forceinline__ void s_add(sacc &s, coef c, val x) {

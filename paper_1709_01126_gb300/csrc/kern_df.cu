@@ -4,8 +4,9 @@
 namespace pot3d {
 
 const MvVariant *mv_variants_df(int *count) {
-  static const MvVariant v[] = {make_variant<PDF, 8, 2, 3>(3), make_variant<PDF, 8, 4, 2>(2)};
-  *count = 2;
+  static const MvVariant v[] = {make_variant<PDF, 8, 2, 3, 3, false>(), make_variant<PDF, 8, 4, 2, 2, false>(),
+                                make_variant<PDF, 16, 2, 3, 1, false>(), make_variant<PDF, 8, 2, 3, 2, false>()};
+  *count = 4;
   return v;
 }
 

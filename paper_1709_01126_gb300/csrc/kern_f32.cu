@@ -4,9 +4,9 @@
 namespace pot3d {
 
 const MvVariant *mv_variants_f32(int *count) {
-  static const MvVariant v[] = {make_variant<PF32, 4, 4, 3>(4), make_variant<PF32, 8, 2, 4>(3),
-                                make_variant<PF32, 8, 4, 3>(2)};
-  *count = 3;
+  static const MvVariant v[] = {make_variant<PF32, 4, 4, 3, 3, true>(), make_variant<PF32, 8, 2, 3, 3, true>(),
+                                make_variant<PF32, 8, 4, 3, 3, true>(), make_variant<PF32, 16, 4, 3, 1, true>()};
+  *count = 4;
   return v;
 }
 

@@ -4,8 +4,9 @@
 namespace pot3d {
 
 const MvVariant *mv_variants_f64(int *count) {
-  static const MvVariant v[] = {make_variant<PF64, 8, 2, 3>(3), make_variant<PF64, 8, 4, 2>(2)};
-  *count = 2;
+  static const MvVariant v[] = {make_variant<PF64, 8, 2, 3, 3, true>(), make_variant<PF64, 8, 4, 2, 2, true>(),
+                                make_variant<PF64, 8, 2, 3, 2, true>()};
+  *count = 3;
   return v;
 }
 

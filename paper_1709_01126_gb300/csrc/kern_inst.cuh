@@ -4,12 +4,12 @@
 
 namespace pot3d {
 
-template <class A, int TJ, int VK, int S>
+template <class A, int TJ, int VK, int S, int MB, bool FP>
 int mv_setup() {
   static int done = 0;
   if (!done) {
     using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
-    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, TJ, VK, S>,
+    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, TJ, VK, S, MB, FP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
     if (e != cudaSuccess) return -3; // POT3D_ERR_CUDA
     done = 1;
@@ -17,15 +17,17 @@ int mv_setup() {
   return 0;
 }
 
-template <class A, int TJ, int VK, int S>
+template <class A, int TJ, int VK, int S, int MB, bool FP>
 void mv_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
                cudaStream_t s) {
   using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
-  k_matvec<A, TJ, VK, S><<<grid, dim3(32, TJ), LY::BYTES, s>>>(probs, work, nwork);
+  k_matvec<A, TJ, VK, S, MB, FP><<<grid, dim3(32, TJ), LY::BYTES, s>>>(probs, work, nwork);
 }
 
-template <class A, int TJ, int VK, int S>
-MvVariant make_variant(int blocks_per_sm) {
+// MB: blocks per SM the launch bounds (and so the register budget) target;
+// FP: separate unchecked code path for tiles inside the grid in phi
+template <class A, int TJ, int VK, int S, int MB, bool FP>
+MvVariant make_variant() {
   using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
   MvVariant v;
   v.tj = TJ;
@@ -37,9 +39,9 @@ MvVariant make_variant(int blocks_per_sm) {
   v.rh = LY::RH;
   v.bw = LY::BW;
   v.smem_bytes = LY::BYTES;
-  v.blocks_per_sm = blocks_per_sm;
-  v.setup = &mv_setup<A, TJ, VK, S>;
-  v.launch = &mv_launch<A, TJ, VK, S>;
+  v.blocks_per_sm = MB;
+  v.setup = &mv_setup<A, TJ, VK, S, MB, FP>;
+  v.launch = &mv_launch<A, TJ, VK, S, MB, FP>;
   return v;
 }
 

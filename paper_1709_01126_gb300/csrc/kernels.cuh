@@ -23,6 +23,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "arith.cuh"
 
 namespace pot3d {
@@ -199,8 +201,8 @@ struct MvLayout {
 // plane), stores p~_new and the deferred x~ += alpha_prev p~_old for its own
 // cells, and applies the stencil to the previous plane (r-neighbours from
 // registers).  The sigma partial closes with the last-block reduction.
-template <class A, int TJ, int VK, int S>
-__global__ void __launch_bounds__(32 * TJ, 3)
+template <class A, int TJ, int VK, int S, int MB, bool FP>
+__global__ void __launch_bounds__(32 * TJ, MB)
     k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
              const int *__restrict__ nwork_p) {
   using val = typename A::val;
@@ -208,18 +210,23 @@ __global__ void __launch_bounds__(32 * TJ, 3)
   using coef = typename A::coef;
   using LY = MvLayout<(int)sizeof(st), TJ, VK, S>;
   constexpr int AL = LY::AL, TK = LY::TK, RH = LY::RH, RW = LY::RW, BW = LY::BW, NT = 32 * TJ;
+  constexpr int ES = (int)sizeof(st);
   extern __shared__ __align__(128) unsigned char smraw[];
   val(*ring)[RH][RW] = reinterpret_cast<val(*)[RH][RW]>(smraw + S * LY::STAGE);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + S * LY::STAGE + LY::RING);
   __shared__ double red[NT / 32];
   __shared__ int s_last;
   const int lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32 + lane;
+  // this thread's first owned cell in ring slot 0; every ring access of the
+  // owned cells and the stencil is a compile-time offset from it
+  val *const rown = &ring[0][wy + 1][lane + 1];
+  constexpr int RPL = RH * RW; // ring plane (elements)
   if (tid == 0) {
     for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t seq = 0; // planes consumed by this block so far (stage/parity counter)
+  uint32_t phase = 0; // bit s: parity of the next completion of stage s's mbarrier
 
   // the work list (and its length) lives in device memory, so one captured
   // graph serves any batch composition
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(32 * TJ, 3)
     st *__restrict__ x = static_cast<st *>(P.x);
     st *__restrict__ q = static_cast<st *>(P.q);
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
-    const size_t R = (size_t)nr * ntp; // table slab of one coefficient
+    const size_t R_ = (size_t)nr * ntp; // table slab of one coefficient
     const typename A::scal beta = A::scal_from(kit > 1 ? ldcg(&stt->beta[(kit - 1) & 1]) : 0.0);
     const typename A::scal alpha_prev =
         A::scal_from(kit > 1 ? ldcg(&stt->alpha[(kit - 1) & 1]) : 0.0);
@@ -253,9 +260,9 @@ __global__ void __launch_bounds__(32 * TJ, 3)
     const int xl = ((np - 1) / AL) * AL, ol = (np - 1) - xl;
     const int ps = max(i0 - 1, 0), pe = min(i1, nr - 1), L = pe - ps + 1;
 
-    auto issue = [&](int tt) {
+    // TMA loads of plane ps + tt into stage sidx (thread 0)
+    auto issue = [&](int tt, int sidx) {
       const int ip = ps + tt;
-      const uint32_t sidx = (seq + tt) % S;
       unsigned char *base = smraw + sidx * LY::STAGE;
       uint64_t *bar = &bars[sidx];
       const bool own = (ip >= i0 && ip < i1);
@@ -281,151 +288,223 @@ __global__ void __launch_bounds__(32 * TJ, 3)
         if (!first) tma_load_3d(base + LY::OFF_PWR, m_pow, bar, 0, j0 - 1, ip);
       }
     };
+    // every tile starts at stage 0: stage of step tt = tt % S
     if (tid == 0) {
-      for (int tt = 0; tt < min(S, L); tt++) issue(tt);
+      for (int tt = 0; tt < min(S, L); tt++) issue(tt, tt);
     }
 
     const int j = j0 + wy;
     const bool jv = j < nt;
+    // full: every owned column k0 .. k0+TK-1 lies inside the grid (no
+    // per-point phi checks); only the last tile column of a row of tiles
+    // is not full.  FP = false keeps only the checked path (half the code:
+    // faster where instruction fetch, not the checks, limits)
+    const bool full = FP && (k0 + TK <= np);
     typename A::dacc tacc = A::d_init();
-    val prv[VK], cur[VK], nxt[VK];
+    // the owned cells of the last three planes: plane ps + tt in R[tt % 3]
+    val R[3][VK];
 #pragma unroll
-    for (int v = 0; v < VK; v++) prv[v] = cur[v] = A::zero();
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+      for (int v = 0; v < VK; v++) R[m][v] = A::zero();
     bool bad = false;
 
+    // Halo cells of the ring (rows 0 and RH-1, columns 0 and RW-1), HPT per
+    // thread, fixed for the tile: byte offset of the r source within a
+    // stage (main box or wrap column; -1: beyond the right wrap column, so
+    // zero), distance from it to the p~_old source, and index within a
+    // ring plane (-1: no cell).
+    constexpr int NH = 2 * RW + 2 * TJ, HPT = (NH + NT - 1) / NT;
+    int h_src[HPT], h_dp[HPT], h_dst[HPT];
+#pragma unroll
+    for (int u = 0; u < HPT; u++) {
+      const int h = tid + u * NT;
+      int rr, cc;
+      if (h < 2 * RW) {
+        rr = (h < RW) ? 0 : RH - 1;
+        cc = (h < RW) ? h : h - RW;
+      } else {
+        const int g = h - 2 * RW;
+        rr = 1 + (g >> 1);
+        cc = (g & 1) ? RW - 1 : 0;
+      }
+      const int kk = k0 - 1 + cc;
+      h_dst[u] = (h < NH) ? rr * RW + cc : -1;
+      if (kk < 0) {
+        h_src[u] = LY::OFF_RWL + (rr * AL + ol) * ES;
+        h_dp[u] = LY::OFF_PWL - LY::OFF_RWL;
+      } else if (kk < np) {
+        h_src[u] = LY::OFF_R + (rr * BW + cc - 1 + AL) * ES;
+        h_dp[u] = LY::OFF_P - LY::OFF_R;
+      } else if (kk == np) {
+        h_src[u] = LY::OFF_RWR + rr * AL * ES;
+        h_dp[u] = LY::OFF_PWR - LY::OFF_RWR;
+      } else {
+        h_src[u] = -1;
+        h_dp[u] = 0;
+      }
+    }
+
+    // stencil of plane i: in-plane neighbours from ring slot SL (a
+    // compile-time constant), r-neighbours from registers (cur, prv, nxt:
+    // planes i, i-1, i+1); F: full tile
     // metric coefficients of row (i, j) for the stencil of the current step
     coef cc_[6];
-    // stencil of plane i from the ring (in-plane neighbours) and registers
-    auto stencil = [&](int i, const coef (&c)[6]) {
-      const int sl = i % 3;
+    auto stencil = [&](int i, const coef(&c)[6], const val(&cur)[VK], const val(&prv)[VK],
+                       const val(&nxt)[VK], auto SL, auto F) {
+      constexpr bool kFull = decltype(F)::value;
+      constexpr int sl = decltype(SL)::value;
       typename A::dacc racc = A::d_init();
-      const size_t rowoff = (size_t)i * plane + (size_t)j * pitch;
+      st *__restrict__ qrow = q + ((size_t)i * plane + (size_t)j * pitch + k0 + lane);
 #pragma unroll
       for (int v = 0; v < VK; v++) {
         const int cc = lane + 32 * v + 1;
         typename A::sacc s = A::s_init(cur[v]);
         A::s_add(s, c[1], nxt[v]);
         A::s_add(s, c[2], prv[v]);
-        A::s_add(s, c[3], ring[sl][wy + 2][cc]);
-        A::s_add(s, c[4], ring[sl][wy][cc]);
-        A::s_add(s, c[5], ring[sl][wy + 1][cc - 1]);
-        A::s_add(s, c[5], ring[sl][wy + 1][cc + 1]);
+        const val *rc = rown + sl * RPL + 32 * v;
+        A::s_add(s, c[3], rc[RW]);
+        A::s_add(s, c[4], rc[-RW]);
+        A::s_add(s, c[5], rc[-1]);
+        A::s_add(s, c[5], rc[1]);
         const val qv = A::s_get(s);
-        const int kk = k0 + cc - 1;
-        if (kk < np) {
-          A::stv(q + rowoff + kk, qv);
+        if (kFull || k0 + cc - 1 < np) {
+          A::stv(qrow + 32 * v, qv);
           A::d_add(racc, cur[v], qv);
         }
       }
       A::d_addw(tacc, c[0], racc);
     };
-
-    int tt = 0;
-    for (; tt < L; tt++) {
-      const int ip = ps + tt;
-      const uint32_t sidx = (seq + tt) % S;
-      const uint32_t parity = ((seq + tt) / S) & 1u;
-      const unsigned char *base = smraw + sidx * LY::STAGE;
+    // p~_new of the owned cells of plane ip into the ring (natural mapping:
+    // warp = theta row, lane = phi), with the stores of p~_new and of the
+    // deferred x~ update for owned planes
+    auto own_cells = [&](int ip, auto SL, bool own, const unsigned char *base, auto F) {
+      constexpr bool kFull = decltype(F)::value;
+      constexpr int sl = decltype(SL)::value;
       const st(*rs)[BW] = reinterpret_cast<const st(*)[BW]>(base + LY::OFF_R);
       const st(*pso)[BW] = reinterpret_cast<const st(*)[BW]>(base + LY::OFF_P);
       const st(*xs)[TK] = reinterpret_cast<const st(*)[TK]>(base + LY::OFF_X);
-      const st(*rwl)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_RWL);
-      const st(*pwl)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_PWL);
       const st(*rwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_RWR);
       const st(*pwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_PWR);
-      const coef(*cs)[TJ] = reinterpret_cast<const coef(*)[TJ]>(base + LY::OFF_C);
-      const int sl = ip % 3;
-      bad = !mbar_wait(&bars[sidx], parity);
+      const int rr = wy + 1;
+      const bool wst = own && jv;
+      const size_t off = (size_t)ip * plane + (size_t)j * pitch + k0 + lane;
+      st *__restrict__ xrow = x + off;
+      st *__restrict__ prow = pnew + off;
 #pragma unroll
-      for (int m = 0; m < 6; m++) cc_[m] = cs[m][wy];
-      const bool own = (ip >= i0 && ip < i1);
-      // owned cells: natural (warp = theta row, lane = phi) mapping
-      {
-        const int rr = wy + 1;
-        const size_t off = (size_t)ip * plane + (size_t)j * pitch;
-#pragma unroll
-        for (int v = 0; v < VK; v++) {
-          const int cc = lane + 32 * v + 1, kk = k0 + cc - 1;
-          val pn = A::zero();
-          if (kk < np) {
-            const val rv = A::ld(&rs[rr][cc - 1 + AL]);
-            if (first) {
-              pn = rv;
-            } else {
-              const val po = A::ld(&pso[rr][cc - 1 + AL]);
-              pn = A::fma(beta, po, rv);
-              if (own && jv) {
-                const val xv = A::ld(&xs[wy][cc - 1]);
-                A::stv(x + off + kk, A::fma(alpha_prev, po, xv));
-              }
-            }
-            if (own && jv) A::stv(pnew + off + kk, pn);
-          } else if (kk == np) {
-            const val rv = A::ld(&rwr[rr][0]);
-            pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
-          }
-          ring[sl][rr][cc] = pn;
-        }
-      }
-      // halo cells: rows 0 and RH-1 (all columns), columns 0 and RW-1
-      for (int h = tid; h < 2 * RW + 2 * TJ; h += NT) {
-        int rr, cc;
-        if (h < 2 * RW) {
-          rr = (h < RW) ? 0 : RH - 1;
-          cc = (h < RW) ? h : h - RW;
-        } else {
-          const int g = h - 2 * RW;
-          rr = 1 + (g >> 1);
-          cc = (g & 1) ? RW - 1 : 0;
-        }
-        const int kk = k0 - 1 + cc;
+      for (int v = 0; v < VK; v++) {
+        const int cc = lane + 32 * v + 1, kk = k0 + cc - 1;
         val pn = A::zero();
-        if (kk < 0) {
-          const val rv = A::ld(&rwl[rr][ol]);
-          pn = first ? rv : A::fma(beta, A::ld(&pwl[rr][ol]), rv);
-        } else if (kk < np) {
+        if (kFull || kk < np) {
           const val rv = A::ld(&rs[rr][cc - 1 + AL]);
-          pn = first ? rv : A::fma(beta, A::ld(&pso[rr][cc - 1 + AL]), rv);
+          if (first) {
+            pn = rv;
+          } else {
+            const val po = A::ld(&pso[rr][cc - 1 + AL]);
+            pn = A::fma(beta, po, rv);
+            if (wst) {
+              const val xv = A::ld(&xs[wy][cc - 1]);
+              A::stv(xrow + 32 * v, A::fma(alpha_prev, po, xv));
+            }
+          }
+          if (wst) A::stv(prow + 32 * v, pn);
         } else if (kk == np) {
           const val rv = A::ld(&rwr[rr][0]);
           pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
         }
-        ring[sl][rr][cc] = pn;
+        rown[sl * RPL + 32 * v] = pn;
+      }
+    };
+
+    // One step per plane, unrolled by the ring period 3 so that ring slots
+    // and the roles of R are compile-time: step tt writes plane ps + tt
+    // into ring slot and R[tt % 3] and applies the stencil to plane
+    // ps + tt - 1 (R[(tt + 2) % 3]; R[(tt + 1) % 3] holds plane ps + tt - 2).
+    int sidx = 0; // stage of step tt
+    auto step = [&](int tt, auto U) -> bool {
+      constexpr int u = decltype(U)::value;
+      using Slot = std::integral_constant<int, u>;
+      using Prev = std::integral_constant<int, (u + 2) % 3>;
+      const int ip = ps + tt;
+      const int st_now = sidx;
+      sidx = (sidx + 1 == S) ? 0 : sidx + 1;
+      const unsigned char *base = smraw + st_now * LY::STAGE;
+      const coef(*cs)[TJ] = reinterpret_cast<const coef(*)[TJ]>(base + LY::OFF_C);
+      bad = !mbar_wait(&bars[st_now], (phase >> st_now) & 1u);
+      if (!bad) phase ^= 1u << st_now;
+#pragma unroll
+      for (int m = 0; m < 6; m++) cc_[m] = cs[m][wy];
+      const bool own = (ip >= i0 && ip < i1);
+      if (full) own_cells(ip, Slot{}, own, base, std::true_type{});
+      else own_cells(ip, Slot{}, own, base, std::false_type{});
+      // halo cells
+      val *ringp = &ring[u][0][0];
+#pragma unroll
+      for (int h = 0; h < HPT; h++) {
+        if (h_dst[h] >= 0) {
+          val pn = A::zero();
+          if (h_src[h] >= 0) {
+            const val rv = A::ld(reinterpret_cast<const st *>(base + h_src[h]));
+            pn = first ? rv
+                       : A::fma(beta, A::ld(reinterpret_cast<const st *>(base + h_src[h] + h_dp[h])),
+                                rv);
+          }
+          ringp[h_dst[h]] = pn;
+        }
       }
       if (__syncthreads_or(bad)) {
         bad = true;
+        return false;
+      }
+      if (tid == 0 && tt + S < L) issue(tt + S, st_now);
+#pragma unroll
+      for (int v = 0; v < VK; v++) R[u][v] = rown[u * RPL + 32 * v];
+      if (ip - 1 >= i0 && jv) {
+        if (full) stencil(ip - 1, cc_, R[(u + 2) % 3], R[(u + 1) % 3], R[u], Prev{}, std::true_type{});
+        else stencil(ip - 1, cc_, R[(u + 2) % 3], R[(u + 1) % 3], R[u], Prev{}, std::false_type{});
+      }
+      return true;
+    };
+    int tt = 0;
+    for (; tt < L; tt += 3) {
+      if (!step(tt, std::integral_constant<int, 0>{})) break;
+      if (tt + 1 < L && !step(tt + 1, std::integral_constant<int, 1>{})) {
+        tt += 1;
         break;
       }
-      if (tid == 0 && tt + S < L) issue(tt + S);
-#pragma unroll
-      for (int v = 0; v < VK; v++) nxt[v] = ring[sl][wy + 1][lane + 32 * v + 1];
-      if (ip - 1 >= i0 && jv) stencil(ip - 1, cc_);
-#pragma unroll
-      for (int v = 0; v < VK; v++) {
-        prv[v] = cur[v];
-        cur[v] = nxt[v];
+      if (tt + 2 < L && !step(tt + 2, std::integral_constant<int, 2>{})) {
+        tt += 2;
+        break;
       }
     }
     if (bad) {
       // drain this tile's transfers still in flight (bounded), then report
       if (tid == 0) {
         for (int u = tt; u < min(L, tt + S); u++)
-          mbar_wait(&bars[(seq + u) % S], ((seq + u) / S) & 1u);
+          mbar_wait(&bars[u % S], (phase >> (u % S)) & 1u);
         stt->status = ST_TIMEOUT;
       }
       __syncthreads();
-      seq += L;
       break;
     }
     if (i1 == nr && jv) {
-#pragma unroll
-      for (int v = 0; v < VK; v++) nxt[v] = A::zero();
+      // plane nr - 1 is the tile's last plane (step L - 1); no plane above
+      const val zero[VK] = {};
       const size_t row = (size_t)(nr - 1) * ntp + j;
 #pragma unroll
-      for (int m = 0; m < 6; m++) cc_[m] = cf[m * R + row];
-      stencil(nr - 1, cc_);
+      for (int m = 0; m < 6; m++) cc_[m] = cf[m * R_ + row];
+      auto last = [&](auto U) {
+        constexpr int u = decltype(U)::value;
+        if (full)
+          stencil(nr - 1, cc_, R[u], R[(u + 2) % 3], zero, U, std::true_type{});
+        else
+          stencil(nr - 1, cc_, R[u], R[(u + 2) % 3], zero, U, std::false_type{});
+      };
+      const int ul = (L - 1) % 3;
+      if (ul == 0) last(std::integral_constant<int, 0>{});
+      else if (ul == 1) last(std::integral_constant<int, 1>{});
+      else last(std::integral_constant<int, 2>{});
     }
-    seq += L;
 
     const double mine = jv ? A::d_get(tacc) : 0.0;
     const double tot = block_sum<NT>(mine, red);

@@ -85,7 +85,7 @@ int stage(Plan *P, size_t bytes);
 void scaled_table(const Plan *P, std::vector<double> &t);
 int encode3d(CUtensorMap *m, void *base, int es, const Plan *P, int bx, int by);
 int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P, int tj);
-int set_decomposition(Plan *P, int ai, int var, int nI);
+int set_decomposition(Plan *P, int ai, int var, int nI, int rows_b);
 int heuristic_chunks(const Plan *P, const MvVariant &v);
 int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
                    const Plan *P);

@@ -213,7 +213,7 @@ int ensure_arith(Plan *P, int ai) {
     return POT3D_ERR_OOM;
   }
   cudaMemset(A.d_state, 0, sizeof(SolveState));
-  rc = set_decomposition(P, ai, 0, 0);
+  rc = set_decomposition(P, ai, 0, 0, 0);
   if (rc) return rc;
   A.ready = true;
   return POT3D_OK;

@@ -104,9 +104,9 @@ int heuristic_chunks(const Plan *P, const MvVariant &v) {
   return std::max(1, std::min(nI, std::max(1, P->nr / 8)));
 }
 
-// Sets the matvec variant and r-chunk count of arithmetic ai and uploads
-// the work lists (one problem: items (0, t)).
-int set_decomposition(Plan *P, int ai, int var, int nI) {
+// Sets the matvec variant, r-chunk count and update rows per item of
+// arithmetic ai and uploads the work lists (one problem: items (0, t)).
+int set_decomposition(Plan *P, int ai, int var, int nI, int rows_b) {
   ArithData &D = P->ar[ai];
   int nv = 0;
   const MvVariant *vs = mv_variants(ai, &nv);
@@ -120,7 +120,7 @@ int set_decomposition(Plan *P, int ai, int var, int nI) {
   D.ic = (P->nr + nI - 1) / nI;
   D.nI = (P->nr + D.ic - 1) / D.ic;
   D.tiles_a = D.nJ * D.nK * D.nI;
-  D.rows_b = kRowsPerUpdateItem;
+  D.rows_b = rows_b > 0 ? rows_b : kRowsPerUpdateItem;
   D.tiles_b = (int)((P->R + D.rows_b - 1) / D.rows_b);
   if (D.tiles_a > D.cap_a) {
     cudaFree(D.d_work_a);
@@ -704,15 +704,18 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int var, nI;
+  int var, nI, rows;
   double ms;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 bool g_tune_loaded = false;
 
-// Optional persistence: POT3D_TUNE_CACHE names a text file of lines
-// "nr nt np arith variant chunks ms".
+// Optional persistence: POT3D_TUNE_CACHE names a text file that starts with
+// the tag kTuneTag, then lines "nr nt np arith variant chunks update_rows
+// matvec_ms".  A file without the tag (another format) is ignored and
+// rewritten.
+constexpr const char *kTuneTag = "pot3d-tune-2";
 void tune_load_locked() {
   if (g_tune_loaded) return;
   g_tune_loaded = true;
@@ -720,9 +723,15 @@ void tune_load_locked() {
   if (!path) return;
   FILE *f = fopen(path, "r");
   if (!f) return;
+  char tag[32] = {0};
+  if (fscanf(f, "%31s", tag) != 1 || strcmp(tag, kTuneTag) != 0) {
+    fclose(f);
+    return;
+  }
   TuneKey k;
   TuneVal v;
-  while (fscanf(f, "%d %d %d %d %d %d %lf", &k.nr, &k.nt, &k.np, &k.ai, &v.var, &v.nI, &v.ms) == 7)
+  while (fscanf(f, "%d %d %d %d %d %d %d %lf", &k.nr, &k.nt, &k.np, &k.ai, &v.var, &v.nI, &v.rows,
+                &v.ms) == 8)
     g_tune[k] = v;
   fclose(f);
 }
@@ -732,9 +741,10 @@ void tune_store_locked() {
   if (!path) return;
   FILE *f = fopen(path, "w");
   if (!f) return;
+  fprintf(f, "%s\n", kTuneTag);
   for (const auto &kv : g_tune)
-    fprintf(f, "%d %d %d %d %d %d %.6f\n", kv.first.nr, kv.first.nt, kv.first.np, kv.first.ai,
-            kv.second.var, kv.second.nI, kv.second.ms);
+    fprintf(f, "%d %d %d %d %d %d %d %.6f\n", kv.first.nr, kv.first.nt, kv.first.np, kv.first.ai,
+            kv.second.var, kv.second.nI, kv.second.rows, kv.second.ms);
   fclose(f);
 }
 
@@ -761,37 +771,69 @@ int tune_arith(Plan *P, int ai, TuneVal *best) {
   int nv = 0;
   const MvVariant *vs = mv_variants(ai, &nv);
   best->ms = INFINITY;
+  best->rows = kRowsPerUpdateItem;
+  auto prepare = [&]() -> int {
+    fill_prob<A>(P, ai, ws_vec(P, 0, es), ws_vec(P, 1, es), ws_vec(P, 2, es), ws_vec(P, 3, es),
+                 ws_vec(P, 4, es));
+    int rc = build_tma(P, ai);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return POT3D_ERR_CUDA;
+    return POT3D_OK;
+  };
+  auto time_kernel = [&](bool matvec, double *avg) -> int {
+    float tot = 0.f;
+    const int warm = 2, reps = 5;
+    for (int it = 0; it < warm + reps; it++) {
+      CTRY(cudaMemcpyAsync(D.d_state, &fake, sizeof(fake), cudaMemcpyHostToDevice, s));
+      CTRY(cudaEventRecord(e0, s));
+      if (matvec) launch_matvec(P, ai);
+      else launch_update(P, ai);
+      CTRY(cudaEventRecord(e1, s));
+      CTRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CTRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (it >= warm) tot += ms;
+    }
+    *avg = tot / reps;
+    return POT3D_OK;
+  };
+  // matvec: tile shape x r-chunks
   for (int v = 0; v < nv; v++) {
     std::vector<int> chunks = {heuristic_chunks(P, vs[v]), 1, 2, 3, 4, 6, 8};
     std::sort(chunks.begin(), chunks.end());
     chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
     for (int nI : chunks) {
       if (nI > std::max(1, P->nr / 4) && nI != 1) continue;
-      int rc = set_decomposition(P, ai, v, nI);
-      if (rc) return rc;
-      fill_prob<A>(P, ai, ws_vec(P, 0, es), ws_vec(P, 1, es), ws_vec(P, 2, es), ws_vec(P, 3, es),
-                   ws_vec(P, 4, es));
-      TRY(build_tma(P, ai));
-      CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
-      float tot = 0.f;
-      const int warm = 2, reps = 5;
-      for (int it = 0; it < warm + reps; it++) {
-        CTRY(cudaMemcpyAsync(D.d_state, &fake, sizeof(fake), cudaMemcpyHostToDevice, s));
-        CTRY(cudaEventRecord(e0, s));
-        launch_matvec(P, ai);
-        CTRY(cudaEventRecord(e1, s));
-        CTRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CTRY(cudaEventElapsedTime(&ms, e0, e1));
-        if (it >= warm) tot += ms;
+      TRY(set_decomposition(P, ai, v, nI, best->rows));
+      TRY(prepare());
+      double avg = 0.0;
+      TRY(time_kernel(true, &avg));
+      if (avg < best->ms) {
+        best->var = v;
+        best->nI = nI;
+        best->ms = avg;
       }
-      const double avg = tot / reps;
-      if (avg < best->ms) *best = TuneVal{v, nI, avg};
     }
   }
+  // update: rows per work item
+  double best_up = INFINITY;
+  int best_rows = kRowsPerUpdateItem;
+  for (int rows : {16, 32, 64, 128}) {
+    TRY(set_decomposition(P, ai, best->var, best->nI, rows));
+    TRY(prepare());
+    double avg = 0.0;
+    TRY(time_kernel(false, &avg));
+    if (avg < best_up) {
+      best_up = avg;
+      best_rows = rows;
+    }
+  }
+  best->rows = best_rows;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return set_decomposition(P, ai, best->var, best->nI);
+  return set_decomposition(P, ai, best->var, best->nI, best->rows);
 }
 
 } // namespace
@@ -803,11 +845,11 @@ extern "C" int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *
   Plan *P = reinterpret_cast<Plan *>(plan);
   if (flags == 0)
     flags = P->prec == POT3D_PREC_FP64 ? 1 : (P->prec == POT3D_PREC_FP64_DF ? 2 : 4);
-  TuneVal last{0, 0, 0.0};
+  TuneVal last{0, 0, 0, 0.0};
   for (int ai = 0; ai < 3; ai++) {
     if (!(flags & (1 << ai))) continue;
     const TuneKey key{P->nr, P->nt, P->np, ai};
-    TuneVal got{0, 0, 0.0};
+    TuneVal got{0, 0, 0, 0.0};
     bool cached = false;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -821,7 +863,7 @@ extern "C" int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *
     int rc;
     if (cached) {
       rc = ensure_arith(P, ai);
-      if (!rc) rc = set_decomposition(P, ai, got.var, got.nI);
+      if (!rc) rc = set_decomposition(P, ai, got.var, got.nI, got.rows);
     } else if (ai == AR_F64) {
       rc = tune_arith<PF64>(P, ai, &got);
     } else if (ai == AR_DF) {
