@@ -11,5 +11,6 @@ const MvVariant *mv_variants_df(int *count) {
 }
 
 KLaunch update_launcher_df() { return &up_launch<PDF>; }
+int update_occupancy_df() { return up_occupancy<PDF>(); }
 
 } // namespace pot3d

@@ -11,12 +11,15 @@ const MvVariant *mv_variants_f32(int *count) {
 }
 
 KLaunch update_launcher_f32() { return &up_launch<PF32>; }
+int update_occupancy_f32() { return up_occupancy<PF32>(); }
 
 // Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
 const MvVariant *mv_variants_f64(int *count);
 const MvVariant *mv_variants_df(int *count);
 KLaunch update_launcher_f64();
 KLaunch update_launcher_df();
+int update_occupancy_f64();
+int update_occupancy_df();
 
 const MvVariant *mv_variants(int ai, int *count) {
   if (ai == 0) return mv_variants_f64(count);
@@ -28,6 +31,12 @@ KLaunch update_launcher(int ai) {
   if (ai == 0) return update_launcher_f64();
   if (ai == 1) return update_launcher_df();
   return update_launcher_f32();
+}
+
+int update_occupancy(int ai) {
+  if (ai == 0) return update_occupancy_f64();
+  if (ai == 1) return update_occupancy_df();
+  return update_occupancy_f32();
 }
 
 } // namespace pot3d

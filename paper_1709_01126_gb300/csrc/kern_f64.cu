@@ -11,5 +11,6 @@ const MvVariant *mv_variants_f64(int *count) {
 }
 
 KLaunch update_launcher_f64() { return &up_launch<PF64>; }
+int update_occupancy_f64() { return up_occupancy<PF64>(); }
 
 } // namespace pot3d

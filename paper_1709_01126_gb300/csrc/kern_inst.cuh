@@ -46,8 +46,7 @@ MvVariant make_variant() {
 }
 
 template <class A>
-void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
-               cudaStream_t s) {
+void up_setup() {
   using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
   static bool done = false;
   if (!done) {
@@ -55,7 +54,28 @@ void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int gri
                          cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
     done = true;
   }
+}
+
+template <class A>
+void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
+               cudaStream_t s) {
+  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
+  up_setup<A>();
   k_update<A, kUpdThreads, kUpdSegBytes><<<grid, kUpdThreads, LY::BYTES, s>>>(probs, work, nwork);
+}
+
+// resident blocks of the update kernel per SM (0 if the query fails)
+template <class A>
+int up_occupancy() {
+  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
+  up_setup<A>();
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<A, kUpdThreads, kUpdSegBytes>,
+                                                    kUpdThreads, LY::BYTES) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 } // namespace pot3d

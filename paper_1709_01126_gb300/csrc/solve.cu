@@ -817,10 +817,17 @@ int tune_arith(Plan *P, int ai, TuneVal *best) {
       }
     }
   }
-  // update: rows per work item
+  // update: rows per work item, fixed sizes and sizes that make whole
+  // waves of resident blocks (no partly filled last wave)
+  std::vector<int> rows_c = {16, 32, 64, 128};
+  const long long nres = (long long)update_occupancy(ai) * P->nsm;
+  for (int k = 1; nres > 0 && k <= 3; k++)
+    rows_c.push_back((int)std::max<long long>(1, ((long long)P->R + k * nres - 1) / (k * nres)));
+  std::sort(rows_c.begin(), rows_c.end());
+  rows_c.erase(std::unique(rows_c.begin(), rows_c.end()), rows_c.end());
   double best_up = INFINITY;
   int best_rows = kRowsPerUpdateItem;
-  for (int rows : {16, 32, 64, 128}) {
+  for (int rows : rows_c) {
     TRY(set_decomposition(P, ai, best->var, best->nI, rows));
     TRY(prepare());
     double avg = 0.0;

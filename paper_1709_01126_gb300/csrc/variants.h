@@ -26,6 +26,8 @@ struct MvVariant {
 const MvVariant *mv_variants(int ai, int *count);
 // The update kernel of arithmetic ai.
 KLaunch update_launcher(int ai);
+// resident blocks per SM of arithmetic ai's update kernel (0: unknown)
+int update_occupancy(int ai);
 
 constexpr int kUpdThreads = 256;
 constexpr int kUpdSegBytes = 2560; // bytes of r (and of q) per warp stage

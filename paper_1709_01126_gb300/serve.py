@@ -94,6 +94,8 @@ def run_batched(requests, inputs, batch_bytes: int, k: int = 16, max_slots: int 
     import torch
 
     plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="mixed") for g in {r.grid for r in requests}}
+    for p in plans.values():
+        p.autotune(4)  # FP32 kernels: tile variant, r-chunks, update rows
     batch = pot3d.Batch(batch_bytes, max_slots=max_slots, inner_tol=inner_tol)
     stats = ServeStats("mixed+batched")
     pending = sorted(requests, key=lambda r: r.arrival)
@@ -132,6 +134,8 @@ def run_fp64_serial(requests, inputs):
     import torch
 
     plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="fp64") for g in {r.grid for r in requests}}
+    for p in plans.values():
+        p.autotune(1)
     stats = ServeStats("fp64 one-at-a-time")
     t0 = time.perf_counter()
     for r in sorted(requests, key=lambda q: q.arrival):
@@ -161,6 +165,7 @@ def calibrate_fp64_rate(grids=GRIDS):
     times = []
     for g in grids:
         plan = pot3d.Plan(*g, ratio=RATIO, precision="fp64")
+        plan.autotune(1)
         br = torch.from_numpy(syn.bipole_br(g[1], g[2], seed=SEED)).cuda()
         phi = torch.empty(g, dtype=torch.float64, device="cuda")
         plan.solve(br, TOL, phi)  # warm
