@@ -158,6 +158,25 @@ int pot3d_last_stats(const pot3d_plan_t *plan, pot3d_stats_t *stats);
  * time in ms measured when the choice was made. */
 int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *chunks, double *ms);
 
+/* Matvec kernel variants of arithmetic `arith` (0 FP64, 1 double-float,
+ * 2 FP32): for variant index `variant`, the tile shape (theta rows x phi
+ * columns), the number of TMA stages and the blocks per SM the kernel's
+ * register budget targets.  Output pointers may be NULL.  Returns
+ * POT3D_ERR_INVALID_ARG when `arith` or `variant` is out of range, so a
+ * caller can enumerate variants 0, 1, ... until it fails. */
+int pot3d_variant_info(int arith, int variant, int *tile_rows, int *tile_cols, int *stages,
+                       int *blocks_per_sm);
+
+/* Manual kernel configuration of arithmetic `arith` on this plan, instead of
+ * pot3d_autotune: matvec variant, r-chunks per tile column (0: heuristic,
+ * clamped to nr) and update rows per work item (0: 32).  Later solves use
+ * it until the next pot3d_autotune or pot3d_set_decomposition.  Every
+ * configuration computes the same operator and iteration; only the
+ * rounding order of the block reductions differs.  POT3D_ERR_INVALID_ARG
+ * for an unknown arithmetic or variant or a negative count. */
+int pot3d_set_decomposition(pot3d_plan_t *plan, int arith, int variant, int chunks,
+                            int update_rows);
+
 /* Device workspace.  By default the plan allocates it with cudaMalloc at
  * the first solve.  A caller that manages device memory itself passes a
  * buffer of at least pot3d_workspace_bytes() bytes, 256-byte aligned; it

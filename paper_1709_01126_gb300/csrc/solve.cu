@@ -891,3 +891,29 @@ extern "C" int pot3d_autotune(pot3d_plan_t *plan, int flags, int *variant, int *
   if (ms) *ms = last.ms;
   return POT3D_OK;
 }
+
+extern "C" int pot3d_variant_info(int arith, int variant, int *tile_rows, int *tile_cols,
+                                  int *stages, int *blocks_per_sm) {
+  if (arith < 0 || arith > 2 || variant < 0) return fail(POT3D_ERR_INVALID_ARG);
+  int nv = 0;
+  const MvVariant *vs = mv_variants(arith, &nv);
+  if (variant >= nv) return fail(POT3D_ERR_INVALID_ARG);
+  if (tile_rows) *tile_rows = vs[variant].tj;
+  if (tile_cols) *tile_cols = vs[variant].tk;
+  if (stages) *stages = vs[variant].stages;
+  if (blocks_per_sm) *blocks_per_sm = vs[variant].blocks_per_sm;
+  return POT3D_OK;
+}
+
+extern "C" int pot3d_set_decomposition(pot3d_plan_t *plan, int arith, int variant, int chunks,
+                                       int update_rows) {
+  if (!plan || arith < 0 || arith > 2 || variant < 0 || chunks < 0 || update_rows < 0)
+    return fail(POT3D_ERR_INVALID_ARG);
+  int nv = 0;
+  mv_variants(arith, &nv);
+  if (variant >= nv) return fail(POT3D_ERR_INVALID_ARG);
+  Plan *P = reinterpret_cast<Plan *>(plan);
+  int rc = ensure_arith(P, arith);
+  if (!rc) rc = set_decomposition(P, arith, variant, chunks, update_rows);
+  return rc ? fail(rc) : POT3D_OK;
+}

@@ -66,7 +66,7 @@ class pot3d_info_t(ctypes.Structure):
                 ("bytes_matvec", ctypes.c_double), ("bytes_update", ctypes.c_double)]
 
 
-EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
+EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_variant_info", "pot3d_set_decomposition", "pot3d_destroy", "pot3d_set_stream", "pot3d_set_opts", "pot3d_get_info",
            "pot3d_last_stats", "pot3d_workspace_bytes", "pot3d_set_workspace", "pot3d_solve",
            "pot3d_solve_mixed", "pot3d_field", "pot3d_apply", "pot3d_residual",
            "pot3d_residual_noalloc", "pot3d_batch_create", "pot3d_batch_destroy",
@@ -79,6 +79,26 @@ _lib = None
 
 def lib_path() -> str:
     return _build.LIB
+
+
+ARITHS = {"fp64": 0, "df": 1, "f32": 2}
+
+
+def _arith(a):
+    return ARITHS[a] if isinstance(a, str) else int(a)
+
+
+def variants(arith):
+    """pot3d_variant_info for every matvec variant of an arithmetic:
+    [{'tile_rows', 'tile_cols', 'stages', 'blocks_per_sm'}, ...]."""
+    out = []
+    L = load()
+    while True:
+        v = [ctypes.c_int(0) for _ in range(4)]
+        if L.pot3d_variant_info(_arith(arith), len(out), *[ctypes.byref(x) for x in v]) != 0:
+            return out
+        out.append(dict(zip(("tile_rows", "tile_cols", "stages", "blocks_per_sm"),
+                            (x.value for x in v))))
 
 
 def load(build_if_missing: bool = False):
@@ -103,6 +123,8 @@ def load(build_if_missing: bool = False):
     L.pot3d_get_info.argtypes = [P, ctypes.POINTER(pot3d_info_t)]
     L.pot3d_last_stats.argtypes = [P, ctypes.POINTER(pot3d_stats_t)]
     L.pot3d_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), D]
+    L.pot3d_variant_info.argtypes = [I, I] + [ctypes.POINTER(I)] * 4
+    L.pot3d_set_decomposition.argtypes = [P, I, I, I, I]
     L.pot3d_workspace_bytes.argtypes = [P]
     L.pot3d_workspace_bytes.restype = ctypes.c_size_t
     L.pot3d_set_workspace.argtypes = [P, V, ctypes.c_size_t]
@@ -233,6 +255,11 @@ class Plan:
         _check(load().pot3d_autotune(self.h, int(flags), ctypes.byref(v), ctypes.byref(c),
                                      ctypes.byref(ms)), "pot3d_autotune")
         return v.value, c.value, ms.value
+
+    def set_decomposition(self, arith, variant, chunks=0, update_rows=0):
+        """pot3d_set_decomposition: arith 'fp64' / 'df' / 'f32' (or 0 / 1 / 2)."""
+        _check(load().pot3d_set_decomposition(self.h, _arith(arith), int(variant), int(chunks),
+                                              int(update_rows)), "pot3d_set_decomposition")
 
     def info(self):
         i = pot3d_info_t()

@@ -284,3 +284,47 @@ def test_explicit_faces_match_oracle(p3, oracle_mod):
         phi = torch.zeros((nr, nt, np_), dtype=torch.float64, device="cuda")
         rc, it = plan.solve(dev(br), 1e-12, phi)
         assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("arith", ["fp64", "df", "f32"])
+def test_every_variant_keeps_parity(p3, oracle_mod, arith):
+    """Every matvec variant, with one and three r-chunks and with 16 and 150
+    update rows per item, on a grid with ragged tails in every dimension
+    for every tile shape (37 theta rows, 150 phi columns), against the
+    oracle's solve."""
+    shape, ratio = (14, 37, 150), 1.03
+    br = make_br("bip", 37, 150)
+    g = oracle_mod.Grid(*shape, ratio=ratio)
+    ref, it_ref, _ = g.solve(br, 1e-12)
+    b = g.rhs(br)
+    prec = {"fp64": "fp64", "df": "df", "f32": "mixed"}[arith]
+    vs = p3.variants(arith)
+    assert len(vs) >= 2
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for v in range(len(vs)):
+        for chunks, rows in ((1, 16), (3, 150)):
+            plan = p3.Plan(*shape, ratio=ratio, precision=prec)
+            plan.set_decomposition(arith, v, chunks, rows)
+            info = plan.info()
+            if arith != "f32":
+                assert info["tiles_update"] == -(-14 * 37 // rows)
+            if prec == "mixed":
+                plan.solve_mixed(dev(br), 1e-11, phi)
+                x = host(phi)
+                assert np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b) <= 1e-11, (v, chunks)
+                assert rel(x, ref) <= 1e-8, (v, chunks)
+            else:
+                rc, it = plan.solve(dev(br), 1e-12, phi)
+                assert abs(it - it_ref) <= 1 and rel(host(phi), ref) <= 1e-9, (v, chunks, it)
+            plan.close()
+
+
+def test_set_decomposition_rejects_bad_arguments(p3):
+    plan = p3.Plan(9, 8, 64)
+    n = len(p3.variants("fp64"))
+    for args in (("fp64", n, 0, 0), ("fp64", -1, 0, 0), (3, 0, 0, 0), ("df", 0, -1, 0),
+                 ("df", 0, 0, -1)):
+        with pytest.raises(p3.Pot3dError):
+            plan.set_decomposition(*args)
+    plan.set_decomposition("df", 0, 100, 1000)  # counts are clamped, not rejected
+    plan.close()
