@@ -98,8 +98,9 @@ typedef struct {
   int use_graphs;     /* 0: automatic (graphs on), 1: on, -1: off                    */
   int time_kernels;   /* 1: time every iteration kernel with CUDA events (no graphs) */
   double inner_tol;   /* MIXED: the inner FP32 PCG hands over to an FP64 refinement
-                         step once its residual fell by this factor (0: 0.1 with
-                         mixed_restart = 0, 1e-4 with mixed_restart = 1)         */
+                         step once its residual fell by this factor (0: with
+                         mixed_restart = 0, 0.5 for grids of 8M unknowns or more
+                         and 0.1 below; with mixed_restart = 1, 1e-4)           */
   int max_outer;      /* MIXED: refinement cap (0: 30 restarts, 200 replacements)    */
   int mixed_restart;  /* MIXED: 0 = after each FP64 step the inner PCG continues on
                          the replaced residual with its search direction kept

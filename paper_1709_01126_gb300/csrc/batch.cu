@@ -243,8 +243,7 @@ void launch_inner_start(Batch *B, int s, double new_scale) {
   k_sum_pairs<kBThreads><<<1, kBThreads, 0, B->stream>>>(S.part_aux, g, B->d_isums + 2 * s);
   const size_t v4 = al(P->npad * 4);
   const bool restart = B->opts.mixed_restart != 0;
-  const double inner_tol =
-      B->opts.inner_tol > 0 ? B->opts.inner_tol : (restart ? 1e-4 : 0.1);
+  const double inner_tol = B->opts.inner_tol > 0 ? B->opts.inner_tol : default_inner_tol(P, restart);
   cudaMemsetAsync(S.v32[0], 0, v4, B->stream);
   if (S.resumable && !restart) {
     S.iter0 = B->h_states[s].iter;

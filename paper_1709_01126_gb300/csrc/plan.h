@@ -90,6 +90,8 @@ int heuristic_chunks(const Plan *P, const MvVariant &v);
 int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
                    const Plan *P);
 int default_maxit(const Plan *P);
+// Inner tolerance of mixed refinement when the options give none.
+double default_inner_tol(const Plan *P, bool restart);
 int segment_cap(const Plan *P);
 
 } // namespace pot3d

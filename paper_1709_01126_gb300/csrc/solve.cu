@@ -104,6 +104,18 @@ int heuristic_chunks(const Plan *P, const MvVariant &v) {
   return std::max(1, std::min(nI, std::max(1, P->nr / 8)));
 }
 
+// Reliable updates: each FP64 residual replacement costs a host round trip
+// (about 0.5-1 ms) plus one FP64 operator application, and the FP32 inner
+// PCG loses less convergence the more often its residual is replaced.  On
+// large grids frequent replacement wins (151x301x601 to 1e-10: 6399 inner
+// iterations, 1.29 s at 0.5 against 7314, 1.44 s at 0.1); on small ones the
+// round trips dominate (81x121x241: 0.088 s at 0.1, 0.102 s at 0.5).
+// Plain restarts need a tight inner solve.
+double default_inner_tol(const Plan *P, bool restart) {
+  if (restart) return 1e-4;
+  return P->n >= 8000000 ? 0.5 : 0.1;
+}
+
 // Sets the matvec variant, r-chunk count and update rows per item of
 // arithmetic ai and uploads the work lists (one problem: items (0, t)).
 int set_decomposition(Plan *P, int ai, int var, int nI, int rows_b) {
@@ -513,8 +525,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   const int gn = aux_grid(P, P->n);
   const float *dinv32 = static_cast<const float *>(D.coef); // slab 0 of the F32 table
   const bool restart = P->opts.mixed_restart != 0;
-  const double inner_tol =
-      P->opts.inner_tol > 0 ? P->opts.inner_tol : (restart ? 1e-4 : 0.1);
+  const double inner_tol = P->opts.inner_tol > 0 ? P->opts.inner_tol : default_inner_tol(P, restart);
   const int max_outer = P->opts.max_outer > 0 ? P->opts.max_outer : (restart ? 30 : 200);
   const int inner_maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
   memset(&P->stats, 0, sizeof(P->stats));
