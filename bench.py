@@ -177,9 +177,38 @@ def cpu_baseline(br, iters=60):
     t = time.perf_counter()
     x, it, st = g.pcg(b, 1e-300, maxit=iters)
     dt = time.perf_counter() - t
-    return {"value": it / dt, "unit": "iters/s", "cores": oracle.get_threads(), "kind": "oracle",
+    cores = oracle.get_threads()
+    # the same oracle on one thread, over a shorter sample
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    x1, it1, st1 = g.pcg(b, 1e-300, maxit=max(2, iters // 10))
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(n)
+    return {"value": it / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
             "sample": "first %d PCG iterations of the 151x301x601 solve (of ~6000 to 1e-10), "
-                      "FP64, OpenMP" % it, "seconds": dt}
+                      "FP64, OpenMP" % it, "seconds": dt,
+            "single_thread": {"value": it1 / dt1, "unit": "iters/s", "cores": 1,
+                              "sample": "first %d PCG iterations" % it1, "seconds": dt1}}
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_151x301x601.json")
+
+
+def sampled_error_vs_oracle(phi):
+    """Relative L2 error of Phi at the sampled points stored with the oracle's
+    own solve of this workload to 1e-10 (None if the file is absent)."""
+    try:
+        with open(GOLDEN) as f:
+            gold = json.load(f)["tol_1e-10"]
+    except (OSError, ValueError, KeyError):
+        return None
+    import numpy as np
+
+    idx = np.asarray(gold["sample_index"], dtype=np.int64)
+    ref = np.asarray(gold["sample_phi"])
+    x = phi.reshape(-1)[idx.tolist()].cpu().numpy()
+    return {"value": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)), "samples": int(idx.size),
+            "source": "tests/golden/oracle_151x301x601.json (oracle PCG to 1e-10)"}
 
 
 def run_reference(args):
@@ -241,6 +270,8 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
         plan.field(phi, br_d, B)
         return it, st
 
+    last = {}
+
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -253,6 +284,7 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
     iters, ka, kb, na, nb, launches = 0, 0.0, 0.0, 0.0, 0.0, 0
     for _ in range(steps):
         it, st = step()
+        last = st
         iters += it
         ka += st["kernel_ms"][0]
         kb += st["kernel_ms"][1]
@@ -297,7 +329,15 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
            "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1], "matvec_ms": tuned[2]},
            "iters_per_solve": iters / steps, "hbm_gbs": value / ws * bytes_per_iter / 1e9,
            "bytes_per_iter": bytes_per_iter, "roofline": roof, "gpu_launches": launches,
-           "clocks": clk, "steps": steps, "warmup": warmup}
+           "clocks": clk, "steps": steps, "warmup": warmup,
+           "final_relres": last.get("relres"),
+           "final_relres_kind": ("FP64 residual recomputed" if prec == "mixed"
+                                 else "PCG recurrence residual")}
+    if prec == "mixed":
+        out["outer_per_solve"] = last.get("outer_iters")
+    err = sampled_error_vs_oracle(phi)
+    if err is not None:
+        out["sampled_rel_error_vs_oracle"] = err
     if with_e2e:
         # end to end through the same C ABI with pinned host buffers
         br_h = torch.from_numpy(br).pin_memory().numpy()

@@ -185,6 +185,8 @@ struct MvLayout {
   static constexpr int STAGE = OFF_C + SZ_C;
   static constexpr int RING = a128(3 * RH * RW * ES);
   static constexpr int BYTES = S * STAGE + RING + 8 * S;
+  // a tensor-map box dimension holds at most 256 elements
+  static_assert(BW <= 256 && RH <= 256, "TMA box wider than 256 elements");
 };
 
 // ------------------------------------------------------------ k_matvec
