@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT_DIR = os.environ.get("POT3D_BUILD_DIR") or os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libpot3d.so")
-# extra nvcc flags, e.g. "-DPOT3D_VK=4" for another matvec tile shape
+# extra nvcc flags (e.g. "-Xptxas -v" to print registers and shared memory)
 EXTRA = os.environ.get("POT3D_NVCC_FLAGS", "").split()
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]

@@ -132,7 +132,6 @@ struct PF64 {
     double v;
   };
   static constexpr int kVec = 2; // elements per 16-byte vector
-  static constexpr bool kFlatUpdate = false; // row sums: one Dinv FMA per row
   static __device__ __forceinline__ val ld(const st *p) { return *p; }
   static __device__ __forceinline__ void stv(st *p, val v) { *p = v; }
   static __device__ __forceinline__ val zero() { return 0.0; }
@@ -170,7 +169,6 @@ struct PDF {
   using sacc = cacc;
   using dacc = cacc;
   static constexpr int kVec = 2;
-  static constexpr bool kFlatUpdate = false;
   static __device__ __forceinline__ val ld(const st *p) {
     float2 t = *p;
     return {t.x, t.y};
@@ -231,7 +229,6 @@ struct PF32 {
   };
   using dacc = cacc; // dot products: exact float products, compensated sums
   static constexpr int kVec = 4;
-  static constexpr bool kFlatUpdate = false;
   static __device__ __forceinline__ val ld(const st *p) { return *p; }
   static __device__ __forceinline__ void stv(st *p, val v) { *p = v; }
   static __device__ __forceinline__ val zero() { return 0.f; }
