@@ -108,6 +108,13 @@ typedef struct {
                          20*(nr+nt+np) iterations ends and the next one
                          restarts); 1 = it always restarts from zero (plain
                          defect correction)                                      */
+  int verify;         /* FP64 and FP64_DF: 0 = stop when the PCG recurrence residual
+                         reaches tol (the paper's stopping rule); 1 = then also
+                         recompute ||b - L Phi|| / ||b|| in FP64 and, while it is
+                         above tol, restart PCG from Phi with that residual (at
+                         most 10 restarts, within max_iters in total).  stats
+                         report the FP64 residual and the restarts (outer_iters).
+                         MIXED always stops on the FP64 residual.                */
 } pot3d_opts_t;
 
 /* Statistics of the last solve on a plan. */

@@ -351,7 +351,7 @@ int pot3d_set_stream(pot3d_plan_t *plan, void *s) {
 int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *o) {
   if (!plan || !o) return fail(POT3D_ERR_INVALID_ARG);
   if (o->max_iters < 0 || o->chunk < 0 || o->inner_tol < 0 || !(o->inner_tol < 1.0) ||
-      o->max_outer < 0)
+      o->max_outer < 0 || o->verify < 0 || o->verify > 1)
     return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);
   P->opts = *o;

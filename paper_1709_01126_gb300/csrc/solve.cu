@@ -607,6 +607,49 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   return status ? fail(status) : POT3D_OK;
 }
 
+// PCG with residual replacement (opts.verify): the recurrence residual of a
+// long solve drifts from the true one (at 401x801x1601 to 1e-10 after ~33k
+// iterations the FP64 result's true residual is 4.2e-10, the double-float
+// one's 7.6e-9).  After each converged run the FP64 residual b - L Phi is
+// recomputed; while it is above tol, PCG restarts from Phi with it (the
+// use_x0 path), within the same iteration cap.
+constexpr int kMaxReplacements = 10;
+
+template <class A>
+static int solve_pcg_verified(Plan *P, int ai, const double *br, double tol, double *phi,
+                              int *iters) {
+  const pot3d_opts_t saved = P->opts;
+  const int cap = saved.max_iters > 0 ? saved.max_iters : default_maxit(P);
+  int total = 0, restarts = 0, rc = POT3D_OK;
+  double rel = 0.0;
+  long long launches = 0;
+  for (;;) {
+    P->opts.max_iters = std::max(1, cap - total);
+    int it = 0;
+    rc = solve_pcg<A>(P, ai, br, tol, phi, &it);
+    total += it;
+    launches += P->stats.launches;
+    if (rc != POT3D_OK) break;
+    rc = pot3d_residual(reinterpret_cast<pot3d_plan_t *>(P), br, phi, &rel);
+    launches += 2;
+    if (rc != POT3D_OK || rel <= tol) break;
+    if (restarts == kMaxReplacements || total >= cap) {
+      rc = POT3D_ERR_NOT_CONVERGED;
+      break;
+    }
+    restarts++;
+    P->opts.use_x0 = 1; // Phi holds the current iterate
+  }
+  P->opts = saved;
+  if (rc == POT3D_OK || rc == POT3D_ERR_NOT_CONVERGED) P->stats.relres = rel;
+  P->stats.status = rc;
+  P->stats.iters = total;
+  P->stats.outer_iters = restarts;
+  P->stats.launches = launches;
+  if (iters) *iters = total;
+  return rc ? fail(rc) : POT3D_OK;
+}
+
 } // namespace pot3d
 
 using namespace pot3d;
@@ -616,9 +659,14 @@ extern "C" {
 int pot3d_solve(pot3d_plan_t *plan, const double *br, double tol, double *phi, int *iters) {
   if (!plan || !br || !phi || !(tol > 0.0) || !std::isfinite(tol)) return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);
+  const bool verify = P->opts.verify != 0;
   switch (P->prec) {
-  case POT3D_PREC_FP64: return solve_pcg<PF64>(P, AR_F64, br, tol, phi, iters);
-  case POT3D_PREC_FP64_DF: return solve_pcg<PDF>(P, AR_DF, br, tol, phi, iters);
+  case POT3D_PREC_FP64:
+    return verify ? solve_pcg_verified<PF64>(P, AR_F64, br, tol, phi, iters)
+                  : solve_pcg<PF64>(P, AR_F64, br, tol, phi, iters);
+  case POT3D_PREC_FP64_DF:
+    return verify ? solve_pcg_verified<PDF>(P, AR_DF, br, tol, phi, iters)
+                  : solve_pcg<PDF>(P, AR_DF, br, tol, phi, iters);
   default: {
     int o = 0, in = 0;
     int rc = solve_mixed(P, br, tol, phi, &o, &in);

@@ -51,7 +51,7 @@ class pot3d_opts_t(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("use_x0", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("mixed_restart", ctypes.c_int)]
+                ("mixed_restart", ctypes.c_int), ("verify", ctypes.c_int)]
 
 
 class pot3d_stats_t(ctypes.Structure):
@@ -240,9 +240,9 @@ class Plan:
             pass
 
     def set_opts(self, max_iters=0, use_x0=0, chunk=0, use_graphs=0, time_kernels=0,
-                 inner_tol=0.0, max_outer=0, mixed_restart=0):
+                 inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0):
         o = pot3d_opts_t(int(max_iters), int(use_x0), int(chunk), int(use_graphs), int(time_kernels),
-                         float(inner_tol), int(max_outer), int(mixed_restart))
+                         float(inner_tol), int(max_outer), int(mixed_restart), int(verify))
         _check(load().pot3d_set_opts(self.h, ctypes.byref(o)), "pot3d_set_opts")
 
     def set_stream(self, stream_handle):
@@ -338,7 +338,7 @@ class Batch:
         self.h = h
         self.max_slots = int(max_slots)
         o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer),
-                         int(mixed_restart))
+                         int(mixed_restart), 0)
         _check(L.pot3d_batch_set_opts(h, ctypes.byref(o)), "pot3d_batch_set_opts")
 
     def close(self):

@@ -82,6 +82,29 @@ def test_c2_full_solve(p3, oracle_mod, c2, prec):
     plan.close()
 
 
+def test_c2_df_verify_restarts_to_true_residual(p3, oracle_mod, c2):
+    """Double-float PCG stopped by its recurrence residual at 1e-10 leaves a
+    true residual slightly above 1e-10 here; with opts.verify it restarts
+    from Phi with the FP64 residual and returns a true residual within tol
+    (recomputed by the oracle)."""
+    g, br, b = c2
+    with open(GOLD) as f:
+        gold = json.load(f)["tol_1e-10"]
+    plan = p3.Plan(*C2, ratio=1.02, precision="df", verify=1)
+    phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(torch.from_numpy(br).cuda(), 1e-10, phi)
+    st = plan.stats()
+    x = phi.cpu().numpy()
+    true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    assert rc == 0 and true_rel <= 1.001e-10, (true_rel, st)
+    assert abs(st["relres"] - true_rel) <= 1e-13
+    assert st["outer_iters"] >= 1 and it > gold["iters"]
+    xs = x.ravel()[gold["sample_index"]]
+    ref = np.array(gold["sample_phi"])
+    assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-9
+    plan.close()
+
+
 def iteration_matches(it, gold, tol, band=0.05):
     """The GPU stops at iteration `it`.  Near the end of this solve the
     residual falls only about 0.4% per iteration, so rounding-order

@@ -328,3 +328,31 @@ def test_set_decomposition_rejects_bad_arguments(p3):
             plan.set_decomposition(*args)
     plan.set_decomposition("df", 0, 100, 1000)  # counts are clamped, not rejected
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("df", 1e-13)])
+def test_verify_stops_on_true_residual(p3, oracle_mod, prec, tol):
+    """opts.verify: the returned Phi's FP64 residual, recomputed by the
+    oracle's own operator, is within tol.  Without verify the solve stops on
+    the recurrence residual; with it the solve restarts from Phi exactly
+    when that left the true residual above tol."""
+    shape, ratio = (17, 35, 129), 1.05
+    br = make_br("bip", 35, 129)
+    g = oracle_mod.Grid(*shape, ratio=ratio)
+    b = g.rhs(br)
+    true_rel = lambda x: np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    plain = p3.Plan(*shape, ratio=ratio, precision=prec)
+    rc0, it0 = plain.solve(dev(br), tol, phi)
+    t0 = true_rel(host(phi))
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec, verify=1)
+    rc, it = plan.solve(dev(br), tol, phi)
+    st = plan.stats()
+    t1 = true_rel(host(phi))
+    assert rc == 0 and t1 <= tol * 1.001, (t0, t1)
+    # both residuals carry FP64 rounding of b - L Phi, about 1e-16 here
+    assert abs(st["relres"] - t1) <= 0.02 * tol
+    if t0 <= tol * 0.999:
+        assert st["outer_iters"] == 0 and it == it0
+    elif t0 > tol * 1.001:
+        assert st["outer_iters"] >= 1 and it > it0
