@@ -198,11 +198,17 @@ struct MvLayout {
 // (TK+2) halo region (x from k0-AL so the box start is 16-byte aligned;
 // theta rows outside the grid arrive zero-filled), of x~ over the owned
 // cells, and of the two periodic wrap columns when the tile touches phi = 0
-// or 2 pi.  S stages run ahead of the compute.  Per plane the block forms
-// p~_new = r + beta p~_old on the region into a 3-plane ring (one barrier per
-// plane), stores p~_new and the deferred x~ += alpha_prev p~_old for its own
-// cells, and applies the stencil to the previous plane (r-neighbours from
-// registers).  The sigma partial closes with the last-block reduction.
+// or 2 pi.  S stages run ahead of the compute; every tile starts at stage 0
+// and each thread tracks one mbarrier parity bit per stage.  Per plane the
+// block forms p~_new = r + beta p~_old on the region into a 3-plane ring (one
+// barrier per plane), stores p~_new and the deferred x~ += alpha_prev p~_old
+// for its own cells, and applies the stencil to the previous plane
+// (r-neighbours from registers).  The plane loop is unrolled by the ring
+// period so ring slots and plane registers are compile-time; tiles inside the
+// grid in phi may take a path without per-point bounds checks (FP); each
+// thread's halo cell offsets are fixed once per tile.  MB sets the launch
+// bounds' blocks per SM (the register budget).  The sigma partial closes with
+// the last-block reduction.
 template <class A, int TJ, int VK, int S, int MB, bool FP>
 __global__ void __launch_bounds__(32 * TJ, MB)
     k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
