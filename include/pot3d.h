@@ -245,6 +245,15 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
 int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, const double *phi,
                            double *relres);
 
+/* Self-test of the device-side wait limit (failure detection without a
+ * fault): one block waits, through the same bounded mbarrier wait the
+ * iteration kernels use, on a barrier that nothing completes, for
+ * limit_s seconds (0 < limit_s <= 10).  *device_status receives the status
+ * the kernel reported, POT3D_ERR_TIMEOUT when the wait gave up as designed;
+ * *elapsed_s (may be NULL) the device time the wait took.  Runs on the legacy
+ * default stream and synchronises it.  Returns POT3D_OK if the test ran. */
+int pot3d_selftest_wait(double limit_s, int *device_status, double *elapsed_s);
+
 /* ---- batched solves (continuous batching) ------------------------------
  * Many solves of different grids advance together in the same persistent
  * kernels: each admitted solve runs the arithmetic of pot3d_solve_mixed

@@ -72,13 +72,22 @@ EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_variant_info", "pot3d_set_deco
            "pot3d_residual_noalloc", "pot3d_batch_create", "pot3d_batch_destroy",
            "pot3d_batch_set_stream", "pot3d_batch_set_opts", "pot3d_batch_bytes_needed",
            "pot3d_batch_submit", "pot3d_batch_step", "pot3d_batch_poll", "pot3d_batch_info",
-           "pot3d_last_error", "pot3d_strerror"]
+           "pot3d_last_error", "pot3d_strerror", "pot3d_selftest_wait"]
 
 _lib = None
 
 
 def lib_path() -> str:
     return _build.LIB
+
+
+def selftest_wait(limit_s: float):
+    """pot3d_selftest_wait: (device status code, elapsed seconds) of a bounded
+    device wait on a barrier that nothing completes."""
+    st, el = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().pot3d_selftest_wait(float(limit_s), ctypes.byref(st), ctypes.byref(el)),
+           "pot3d_selftest_wait")
+    return st.value, el.value
 
 
 ARITHS = {"fp64": 0, "df": 1, "f32": 2}
@@ -148,6 +157,8 @@ def load(build_if_missing: bool = False):
                                    ctypes.POINTER(I), ctypes.POINTER(I), D, I, ctypes.POINTER(I)]
     L.pot3d_batch_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)]
+    L.pot3d_selftest_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double)]
     L.pot3d_last_error.argtypes = []
     L.pot3d_strerror.argtypes = [I]
     L.pot3d_strerror.restype = ctypes.c_char_p

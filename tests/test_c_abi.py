@@ -54,3 +54,12 @@ def test_strerror_and_errors_without_gpu(lib):
                                 ctypes.c_void_p, ctypes.c_void_p]
     assert lib.pot3d_solve(None, None, 1e-10, None, None) == -1
     assert lib.pot3d_last_error() == -1
+
+
+def test_selftest_wait_validates_before_any_cuda_call(lib):
+    lib.pot3d_selftest_wait.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    st = ctypes.c_int(7)
+    for limit in (0.0, -1.0, 11.0, float("nan")):
+        assert lib.pot3d_selftest_wait(limit, ctypes.byref(st), None) == -1
+    assert lib.pot3d_selftest_wait(0.1, None, None) == -1
+    assert st.value == 7
