@@ -211,6 +211,16 @@ def sampled_error_vs_oracle(phi):
             "source": "tests/golden/oracle_151x301x601.json (oracle PCG to 1e-10)"}
 
 
+def workload_config(prec, ws):
+    """The benchmark workload, identical on the GPU arm and the reference arm."""
+    return {"workload": "potential-field PCG 151x301x601, r geometric 1.02, "
+                        "dipole + 200 bipoles (seed 1709), tol 1e-10, + field",
+            "grid": list(SHAPE), "tol": TOL, "precision": prec,
+            "l2": "inputs larger than L2 (each vector %.0f MB)"
+                  % ((4 if prec == "mixed" else 8) * SHAPE[0] * SHAPE[1] * SHAPE[2] / 1e6),
+            "parallelism": "replicas x%d" % ws}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     dist = dist_init("gloo")
@@ -238,11 +248,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "151x301x601 FP64 Jacobi PCG (oracle on host cores); one "
-                                   "step = %d iterations of the solve" % per_step},
+            "config": workload_config(args.prec, 1),
             "cpu_baseline": {"value": v, "unit": "iters/s", "kind": "oracle",
                              "cores": oracle.get_threads(),
-                             "sample": "%d PCG iterations per step" % per_step},
+                             "sample": "each step: the first %d PCG iterations of this solve "
+                                       "(FP64 oracle, OpenMP)" % per_step},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -399,13 +409,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
         "data": "synthetic",
-        "config": {"workload": "potential-field PCG 151x301x601, r geometric 1.02, "
-                               "dipole + 200 bipoles (seed 1709), tol 1e-10, + field",
-                   "grid": list(SHAPE), "tol": TOL, "precision": args.prec,
-                   "iters_per_solve": head["iters_per_solve"],
-                   "l2": "inputs larger than L2 (each vector %.0f MB)"
-                         % ((4 if args.prec == "mixed" else 8) * SHAPE[0] * SHAPE[1] * SHAPE[2] / 1e6),
-                   "parallelism": "replicas x%d" % ws},
+        "config": dict(workload_config(args.prec, ws), iters_per_solve=head["iters_per_solve"]),
         "hbm_gbs": head["hbm_gbs"], "bytes_per_iter": head["bytes_per_iter"],
         "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
         "autotune": head["autotune"],
