@@ -147,7 +147,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
 # captures summarised in profiles/k_matvec_k_update_151x301x601.md (same
 # kernels and tuned configuration as timed here)
-TRAFFIC = {"fp64": 1.2932e9, "df": 1.2850e9, "mixed": 0.6196e9}
+TRAFFIC = {"fp64": 1.2927e9, "df": 1.2851e9, "mixed": 0.6223e9}
 
 # FP64 FMA units: 152 SMs x 2 per clock at the 2070 MHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12

@@ -5,8 +5,9 @@ namespace pot3d {
 
 const MvVariant *mv_variants_f32(int *count) {
   static const MvVariant v[] = {make_variant<PF32, 4, 4, 3, 3, true>(), make_variant<PF32, 8, 2, 3, 3, true>(),
-                                make_variant<PF32, 8, 4, 3, 3, true>(), make_variant<PF32, 16, 4, 3, 1, true>()};
-  *count = 4;
+                                make_variant<PF32, 8, 4, 3, 3, true>(), make_variant<PF32, 16, 4, 3, 1, true>(),
+                                make_variant<PF32, 16, 4, 2, 2, true, 2>()};
+  *count = 5;
   return v;
 }
 

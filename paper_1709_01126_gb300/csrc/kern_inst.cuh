@@ -4,12 +4,12 @@
 
 namespace pot3d {
 
-template <class A, int TJ, int VK, int S, int MB, bool FP>
+template <class A, int TJ, int VK, int S, int MB, bool FP, int RPW>
 int mv_setup() {
   static int done = 0;
   if (!done) {
     using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
-    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, TJ, VK, S, MB, FP>,
+    cudaError_t e = cudaFuncSetAttribute(k_matvec<A, TJ, VK, S, MB, FP, RPW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
     if (e != cudaSuccess) return -3; // POT3D_ERR_CUDA
     done = 1;
@@ -17,16 +17,17 @@ int mv_setup() {
   return 0;
 }
 
-template <class A, int TJ, int VK, int S, int MB, bool FP>
+template <class A, int TJ, int VK, int S, int MB, bool FP, int RPW>
 void mv_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
                cudaStream_t s) {
   using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
-  k_matvec<A, TJ, VK, S, MB, FP><<<grid, dim3(32, TJ), LY::BYTES, s>>>(probs, work, nwork);
+  k_matvec<A, TJ, VK, S, MB, FP, RPW><<<grid, dim3(32, TJ / RPW), LY::BYTES, s>>>(probs, work, nwork);
 }
 
 // MB: blocks per SM the launch bounds (and so the register budget) target;
-// FP: separate unchecked code path for tiles inside the grid in phi
-template <class A, int TJ, int VK, int S, int MB, bool FP>
+// FP: separate unchecked code path for tiles inside the grid in phi;
+// RPW: theta rows per warp (TJ / RPW warps per block)
+template <class A, int TJ, int VK, int S, int MB, bool FP, int RPW = 1>
 MvVariant make_variant() {
   using LY = MvLayout<(int)sizeof(typename A::st), TJ, VK, S>;
   MvVariant v;
@@ -40,8 +41,8 @@ MvVariant make_variant() {
   v.bw = LY::BW;
   v.smem_bytes = LY::BYTES;
   v.blocks_per_sm = MB;
-  v.setup = &mv_setup<A, TJ, VK, S, MB, FP>;
-  v.launch = &mv_launch<A, TJ, VK, S, MB, FP>;
+  v.setup = &mv_setup<A, TJ, VK, S, MB, FP, RPW>;
+  v.launch = &mv_launch<A, TJ, VK, S, MB, FP, RPW>;
   return v;
 }
 

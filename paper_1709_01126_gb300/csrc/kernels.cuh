@@ -213,15 +213,17 @@ struct MvLayout {
 // thread's halo cell offsets are fixed once per tile.  MB sets the launch
 // bounds' blocks per SM (the register budget).  The sigma partial closes with
 // the last-block reduction.
-template <class A, int TJ, int VK, int S, int MB, bool FP>
-__global__ void __launch_bounds__(32 * TJ, MB)
+template <class A, int TJ, int VK, int S, int MB, bool FP, int RPW>
+__global__ void __launch_bounds__(32 * (TJ / RPW), MB)
     k_matvec(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
              const int *__restrict__ nwork_p) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
   using LY = MvLayout<(int)sizeof(st), TJ, VK, S>;
-  constexpr int AL = LY::AL, TK = LY::TK, RH = LY::RH, RW = LY::RW, BW = LY::BW, NT = 32 * TJ;
+  static_assert(TJ % RPW == 0, "a warp owns RPW whole theta rows");
+  constexpr int AL = LY::AL, TK = LY::TK, RH = LY::RH, RW = LY::RW, BW = LY::BW;
+  constexpr int NT = 32 * (TJ / RPW);
   constexpr int ES = (int)sizeof(st);
   extern __shared__ __align__(128) unsigned char smraw[];
   val(*ring)[RH][RW] = reinterpret_cast<val(*)[RH][RW]>(smraw + S * LY::STAGE);
@@ -231,7 +233,8 @@ __global__ void __launch_bounds__(32 * TJ, MB)
   const int lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32 + lane;
   // this thread's first owned cell in ring slot 0; every ring access of the
   // owned cells and the stencil is a compile-time offset from it
-  val *const rown = &ring[0][wy + 1][lane + 1];
+  // (row wy * RPW; its other rows follow at RW)
+  val *const rown = &ring[0][wy * RPW + 1][lane + 1];
   constexpr int RPL = RH * RW; // ring plane (elements)
   if (tid == 0) {
     for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
@@ -305,8 +308,8 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       for (int tt = 0; tt < min(S, L); tt++) issue(tt, tt);
     }
 
-    const int j = j0 + wy;
-    const bool jv = j < nt;
+    // theta rows of this warp: j0 + wy * RPW + rr, rr < RPW
+    const int jw = j0 + wy * RPW;
     // full: every owned column k0 .. k0+TK-1 lies inside the grid (no
     // per-point phi checks); only the last tile column of a row of tiles
     // is not full.  FP = false keeps only the checked path (half the code:
@@ -314,11 +317,13 @@ __global__ void __launch_bounds__(32 * TJ, MB)
     const bool full = FP && (k0 + TK <= np);
     typename A::dacc tacc = A::d_init();
     // the owned cells of the last three planes: plane ps + tt in R[tt % 3]
-    val R[3][VK];
+    val R[3][RPW][VK];
 #pragma unroll
     for (int m = 0; m < 3; m++)
 #pragma unroll
-      for (int v = 0; v < VK; v++) R[m][v] = A::zero();
+      for (int rr = 0; rr < RPW; rr++)
+#pragma unroll
+        for (int v = 0; v < VK; v++) R[m][rr][v] = A::zero();
     bool bad = false;
 
     // Halo cells of the ring (rows 0 and RH-1, columns 0 and RW-1), HPT per
@@ -357,24 +362,24 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       }
     }
 
-    // stencil of plane i: in-plane neighbours from ring slot SL (a
-    // compile-time constant), r-neighbours from registers (cur, prv, nxt:
+    // stencil of plane i, row jw + rr: in-plane neighbours from ring slot SL
+    // (a compile-time constant), r-neighbours from registers (cur, prv, nxt:
     // planes i, i-1, i+1); F: full tile
-    // metric coefficients of row (i, j) for the stencil of the current step
-    coef cc_[6];
-    auto stencil = [&](int i, const coef(&c)[6], const val(&cur)[VK], const val(&prv)[VK],
-                       const val(&nxt)[VK], auto SL, auto F) {
+    // metric coefficients of rows (i, jw + rr) for the stencil of the current step
+    coef cc_[RPW][6];
+    auto stencil = [&](int i, int rr, const coef(&c)[6], const val(&cur)[VK],
+                       const val(&prv)[VK], const val(&nxt)[VK], auto SL, auto F) {
       constexpr bool kFull = decltype(F)::value;
       constexpr int sl = decltype(SL)::value;
       typename A::dacc racc = A::d_init();
-      st *__restrict__ qrow = q + ((size_t)i * plane + (size_t)j * pitch + k0 + lane);
+      st *__restrict__ qrow = q + ((size_t)i * plane + (size_t)(jw + rr) * pitch + k0 + lane);
 #pragma unroll
       for (int v = 0; v < VK; v++) {
         const int cc = lane + 32 * v + 1;
         typename A::sacc s = A::s_init(cur[v]);
         A::s_add(s, c[1], nxt[v]);
         A::s_add(s, c[2], prv[v]);
-        const val *rc = rown + sl * RPL + 32 * v;
+        const val *rc = rown + sl * RPL + rr * RW + 32 * v;
         A::s_add(s, c[3], rc[RW]);
         A::s_add(s, c[4], rc[-RW]);
         A::s_add(s, c[5], rc[-1]);
@@ -398,33 +403,37 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       const st(*xs)[TK] = reinterpret_cast<const st(*)[TK]>(base + LY::OFF_X);
       const st(*rwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_RWR);
       const st(*pwr)[AL] = reinterpret_cast<const st(*)[AL]>(base + LY::OFF_PWR);
-      const int rr = wy + 1;
-      const bool wst = own && jv;
-      const size_t off = (size_t)ip * plane + (size_t)j * pitch + k0 + lane;
-      st *__restrict__ xrow = x + off;
-      st *__restrict__ prow = pnew + off;
 #pragma unroll
-      for (int v = 0; v < VK; v++) {
-        const int cc = lane + 32 * v + 1, kk = k0 + cc - 1;
-        val pn = A::zero();
-        if (kFull || kk < np) {
-          const val rv = A::ld(&rs[rr][cc - 1 + AL]);
-          if (first) {
-            pn = rv;
-          } else {
-            const val po = A::ld(&pso[rr][cc - 1 + AL]);
-            pn = A::fma(beta, po, rv);
-            if (wst) {
-              const val xv = A::ld(&xs[wy][cc - 1]);
-              A::stv(xrow + 32 * v, A::fma(alpha_prev, po, xv));
+      for (int w = 0; w < RPW; w++) {
+        const int tr = wy * RPW + w; // tile row
+        const int rr = tr + 1;       // halo-box / ring row
+        const bool wst = own && (jw + w < nt);
+        const size_t off = (size_t)ip * plane + (size_t)(jw + w) * pitch + k0 + lane;
+        st *__restrict__ xrow = x + off;
+        st *__restrict__ prow = pnew + off;
+#pragma unroll
+        for (int v = 0; v < VK; v++) {
+          const int cc = lane + 32 * v + 1, kk = k0 + cc - 1;
+          val pn = A::zero();
+          if (kFull || kk < np) {
+            const val rv = A::ld(&rs[rr][cc - 1 + AL]);
+            if (first) {
+              pn = rv;
+            } else {
+              const val po = A::ld(&pso[rr][cc - 1 + AL]);
+              pn = A::fma(beta, po, rv);
+              if (wst) {
+                const val xv = A::ld(&xs[tr][cc - 1]);
+                A::stv(xrow + 32 * v, A::fma(alpha_prev, po, xv));
+              }
             }
+            if (wst) A::stv(prow + 32 * v, pn);
+          } else if (kk == np) {
+            const val rv = A::ld(&rwr[rr][0]);
+            pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
           }
-          if (wst) A::stv(prow + 32 * v, pn);
-        } else if (kk == np) {
-          const val rv = A::ld(&rwr[rr][0]);
-          pn = first ? rv : A::fma(beta, A::ld(&pwr[rr][0]), rv);
+          rown[sl * RPL + w * RW + 32 * v] = pn;
         }
-        rown[sl * RPL + 32 * v] = pn;
       }
     };
 
@@ -445,7 +454,9 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       bad = !mbar_wait(&bars[st_now], (phase >> st_now) & 1u);
       if (!bad) phase ^= 1u << st_now;
 #pragma unroll
-      for (int m = 0; m < 6; m++) cc_[m] = cs[m][wy];
+      for (int w = 0; w < RPW; w++)
+#pragma unroll
+        for (int m = 0; m < 6; m++) cc_[w][m] = cs[m][wy * RPW + w];
       const bool own = (ip >= i0 && ip < i1);
       if (full) own_cells(ip, Slot{}, own, base, std::true_type{});
       else own_cells(ip, Slot{}, own, base, std::false_type{});
@@ -470,10 +481,20 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       }
       if (tid == 0 && tt + S < L) issue(tt + S, st_now);
 #pragma unroll
-      for (int v = 0; v < VK; v++) R[u][v] = rown[u * RPL + 32 * v];
-      if (ip - 1 >= i0 && jv) {
-        if (full) stencil(ip - 1, cc_, R[(u + 2) % 3], R[(u + 1) % 3], R[u], Prev{}, std::true_type{});
-        else stencil(ip - 1, cc_, R[(u + 2) % 3], R[(u + 1) % 3], R[u], Prev{}, std::false_type{});
+      for (int w = 0; w < RPW; w++)
+#pragma unroll
+        for (int v = 0; v < VK; v++) R[u][w][v] = rown[u * RPL + w * RW + 32 * v];
+      if (ip - 1 >= i0) {
+#pragma unroll
+        for (int w = 0; w < RPW; w++) {
+          if (jw + w >= nt) break;
+          if (full)
+            stencil(ip - 1, w, cc_[w], R[(u + 2) % 3][w], R[(u + 1) % 3][w], R[u][w], Prev{},
+                    std::true_type{});
+          else
+            stencil(ip - 1, w, cc_[w], R[(u + 2) % 3][w], R[(u + 1) % 3][w], R[u][w], Prev{},
+                    std::false_type{});
+        }
       }
       return true;
     };
@@ -499,18 +520,25 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       __syncthreads();
       break;
     }
-    if (i1 == nr && jv) {
+    if (i1 == nr) {
       // plane nr - 1 is the tile's last plane (step L - 1); no plane above
       const val zero[VK] = {};
-      const size_t row = (size_t)(nr - 1) * ntp + j;
 #pragma unroll
-      for (int m = 0; m < 6; m++) cc_[m] = cf[m * R_ + row];
+      for (int w = 0; w < RPW; w++) {
+        const size_t row = (size_t)(nr - 1) * ntp + (jw + w < nt ? jw + w : 0);
+#pragma unroll
+        for (int m = 0; m < 6; m++) cc_[w][m] = cf[m * R_ + row];
+      }
       auto last = [&](auto U) {
         constexpr int u = decltype(U)::value;
-        if (full)
-          stencil(nr - 1, cc_, R[u], R[(u + 2) % 3], zero, U, std::true_type{});
-        else
-          stencil(nr - 1, cc_, R[u], R[(u + 2) % 3], zero, U, std::false_type{});
+#pragma unroll
+        for (int w = 0; w < RPW; w++) {
+          if (jw + w >= nt) break;
+          if (full)
+            stencil(nr - 1, w, cc_[w], R[u][w], R[(u + 2) % 3][w], zero, U, std::true_type{});
+          else
+            stencil(nr - 1, w, cc_[w], R[u][w], R[(u + 2) % 3][w], zero, U, std::false_type{});
+        }
       };
       const int ul = (L - 1) % 3;
       if (ul == 0) last(std::integral_constant<int, 0>{});
@@ -518,7 +546,8 @@ __global__ void __launch_bounds__(32 * TJ, MB)
       else last(std::integral_constant<int, 2>{});
     }
 
-    const double mine = jv ? A::d_get(tacc) : 0.0;
+    // rows beyond nt never accumulated into tacc
+    const double mine = A::d_get(tacc);
     const double tot = block_sum<NT>(mine, red);
     if (tid == 0) {
       P.part_a[t] = tot;
