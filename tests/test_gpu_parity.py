@@ -1,5 +1,5 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
-the same seeded inputs.  Bar (BASELINE the benchmark spec): Phi relative L2 <= 1e-9
+the same seeded inputs.  Bar: Phi relative L2 <= 1e-9
 at relative residual 1e-12, iteration counts within +-1; the operator and
 the field elementwise to FP64 rounding."""
 import numpy as np
