@@ -572,7 +572,7 @@ def run_large_solve(args):
     out = {}
     for prec in [p for p in args.large_precs.split(",") if p]:
         plan = pot3d.Plan(*shape, ratio=args.large_ratio, precision=prec,
-                          max_iters=args.large_maxit)
+                          max_iters=args.large_maxit, verify=1 if args.large_verify else 0)
         tuned = plan.autotune(4 if prec == "mixed" else 0)
         phi.zero_()
         torch.cuda.synchronize()
@@ -584,7 +584,10 @@ def run_large_solve(args):
             outer = 0
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
+        if prec != "mixed":
+            outer = plan.stats()["outer_iters"]  # residual replacements (verify)
         out[prec] = {"status": rc, "seconds": dt, "iters": it, "outer": outer,
+                     "verify": bool(args.large_verify) and prec != "mixed",
                      "iters_per_s": it / dt, "relres_fp64": plan.residual(br_d, phi),
                      "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1]}}
         plan.close()
@@ -619,6 +622,8 @@ def main():
                     help="precisions of --workload large-solve, comma-separated")
     ap.add_argument("--large-ratio", type=float, default=RATIO)
     ap.add_argument("--large-maxit", type=int, default=60000)
+    ap.add_argument("--large-verify", action="store_true",
+                    help="large-solve: FP64/double-float restart on the FP64 residual (opts.verify)")
     ap.add_argument("--large-iters", type=int, default=200)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--batch-k", type=int, default=16)
