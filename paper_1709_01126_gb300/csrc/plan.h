@@ -58,7 +58,8 @@ struct Plan {
   double *d_part = nullptr;
   double *d_sums = nullptr;
   double *h_sums = nullptr;    // pinned [8]
-  SolveState *h_state = nullptr; // pinned
+  SolveState *h_state = nullptr; // pinned, two snapshots: [0] is the final state of a solve
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   double *d_br_last = nullptr;
   bool have_br = false;
   double *d_stage = nullptr;

@@ -55,8 +55,9 @@ int plan_device_init(Plan *P) {
   CTRY(cudaMalloc(&P->d_part, sizeof(double) * 2 * P->aux_blocks));
   CTRY(cudaMalloc(&P->d_sums, sizeof(double) * 8));
   CTRY(cudaMallocHost(&P->h_sums, sizeof(double) * 8));
-  CTRY(cudaMallocHost(&P->h_state, sizeof(SolveState)));
-  memset(P->h_state, 0, sizeof(SolveState));
+  CTRY(cudaMallocHost(&P->h_state, 2 * sizeof(SolveState)));
+  memset(P->h_state, 0, 2 * sizeof(SolveState));
+  for (auto &e : P->poll_ev) CTRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return POT3D_OK;
 }
 
@@ -75,6 +76,8 @@ void plan_free(Plan *P) {
     cudaFree(A.d_nwork);
   }
   for (auto e : P->ev) cudaEventDestroy(e);
+  for (auto e : P->poll_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(P->d_c64);
   cudaFree(P->d_S);
   cudaFree(P->d_irs);
@@ -287,56 +290,89 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
     }
   }
   int done_before = iter0, last_iter = iter0 - 1;
-  for (;;) {
-    if (timing) {
+  if (!timing) {
+    // Chunks as one graph (or plain launches), with one chunk always queued
+    // ahead of the host's poll: the state snapshot of chunk N is read (event)
+    // while chunk N+1 runs, so the GPU does not idle on the round trip.  A
+    // chunk queued after the solve stopped does nothing (its kernels see the
+    // status and exit).
+    if (graphs && (!D.graph || D.graph_chunk != chunk)) {
+      if (D.graph) cudaGraphExecDestroy(D.graph);
+      D.graph = nullptr;
+      cudaGraph_t g;
+      CTRY(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
       for (int c = 0; c < chunk; c++) {
-        CTRY(cudaEventRecord(P->ev[3 * c], P->stream));
         launch_matvec(P, ai);
-        CTRY(cudaEventRecord(P->ev[3 * c + 1], P->stream));
         launch_update(P, ai);
-        CTRY(cudaEventRecord(P->ev[3 * c + 2], P->stream));
       }
-    } else if (graphs) {
-      if (!D.graph || D.graph_chunk != chunk) {
-        if (D.graph) cudaGraphExecDestroy(D.graph);
-        D.graph = nullptr;
-        cudaGraph_t g;
-        CTRY(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+      CTRY(cudaStreamEndCapture(P->stream, &g));
+      cudaError_t e = cudaGraphInstantiate(&D.graph, g, 0);
+      cudaGraphDestroy(g);
+      CTRY(e);
+      D.graph_chunk = chunk;
+    }
+    SolveState *snap[2] = {P->h_state, P->h_state + 1};
+    auto enqueue = [&](int b) -> int {
+      if (graphs) {
+        CTRY(cudaGraphLaunch(D.graph, P->stream));
+      } else {
         for (int c = 0; c < chunk; c++) {
           launch_matvec(P, ai);
           launch_update(P, ai);
         }
-        CTRY(cudaStreamEndCapture(P->stream, &g));
-        cudaError_t e = cudaGraphInstantiate(&D.graph, g, 0);
-        cudaGraphDestroy(g);
-        CTRY(e);
-        D.graph_chunk = chunk;
       }
-      CTRY(cudaGraphLaunch(D.graph, P->stream));
-    } else {
-      for (int c = 0; c < chunk; c++) {
-        launch_matvec(P, ai);
-        launch_update(P, ai);
+      CTRY(cudaGetLastError());
+      P->stats.launches += 2LL * chunk;
+      CTRY(cudaMemcpyAsync(snap[b], D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                           P->stream));
+      CTRY(cudaEventRecord(P->poll_ev[b], P->stream));
+      return POT3D_OK;
+    };
+    int b = 0;
+    TRY(enqueue(0));
+    for (;;) {
+      TRY(enqueue(b ^ 1));
+      CTRY(cudaEventSynchronize(P->poll_ev[b]));
+      if (snap[b]->status != ST_RUNNING) break;
+      // a running solve must advance every chunk; if it does not, the
+      // device state is inconsistent: stop instead of polling forever
+      if (snap[b]->iter <= last_iter) {
+        cudaStreamSynchronize(P->stream);
+        return fail(POT3D_ERR_TIMEOUT);
       }
+      last_iter = snap[b]->iter;
+      b ^= 1;
+    }
+    // the last queued chunk saw the finished state; its snapshot is final
+    CTRY(cudaStreamSynchronize(P->stream));
+    if (b == 0) *snap[0] = *snap[1];
+    return POT3D_OK;
+  }
+  // time_kernels: plain launches between CUDA events, one chunk at a time
+  for (;;) {
+    for (int c = 0; c < chunk; c++) {
+      CTRY(cudaEventRecord(P->ev[3 * c], P->stream));
+      launch_matvec(P, ai);
+      CTRY(cudaEventRecord(P->ev[3 * c + 1], P->stream));
+      launch_update(P, ai);
+      CTRY(cudaEventRecord(P->ev[3 * c + 2], P->stream));
     }
     CTRY(cudaGetLastError());
     P->stats.launches += 2LL * chunk;
     CTRY(cudaMemcpyAsync(P->h_state, D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                          P->stream));
     CTRY(cudaStreamSynchronize(P->stream));
-    if (timing) {
-      // only iterations that did work count (kernels exit early once done)
-      const int real = std::min(chunk, P->h_state->iter - done_before);
-      done_before = P->h_state->iter;
-      for (int c = 0; c < real; c++) {
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, P->ev[3 * c], P->ev[3 * c + 1]);
-        cudaEventElapsedTime(&b, P->ev[3 * c + 1], P->ev[3 * c + 2]);
-        P->stats.kernel_ms[0] += a;
-        P->stats.kernel_ms[1] += b;
-        P->stats.kernel_ms[2] += 1.0;
-        P->stats.kernel_ms[3] += 1.0;
-      }
+    // only iterations that did work count (kernels exit early once done)
+    const int real = std::min(chunk, P->h_state->iter - done_before);
+    done_before = P->h_state->iter;
+    for (int c = 0; c < real; c++) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, P->ev[3 * c], P->ev[3 * c + 1]);
+      cudaEventElapsedTime(&b, P->ev[3 * c + 1], P->ev[3 * c + 2]);
+      P->stats.kernel_ms[0] += a;
+      P->stats.kernel_ms[1] += b;
+      P->stats.kernel_ms[2] += 1.0;
+      P->stats.kernel_ms[3] += 1.0;
     }
     if (P->h_state->status != ST_RUNNING) break;
     // a running solve must advance every chunk; if it does not, the
