@@ -150,7 +150,29 @@ def measured_peaks():
 TRAFFIC = {"fp64": 1.2927e9, "df": 1.2851e9, "mixed": 0.6223e9}
 
 # FP64 FMA units: 152 SMs x 2 per clock at the 2070 MHz maximum SM clock
+# (nominal; the roofline uses the rate measured by pot3d_probe_fp64_fma)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+HBM_NOMINAL_GBS = 7900.0
+
+_fp64_peak = None
+
+
+def fp64_peak(pot3d):
+    """Measured FP64 peak (TFLOP/s) from the library's DFMA throughput probe,
+    with the SM clock sampled while it ran; measured once per process."""
+    global _fp64_peak
+    if _fp64_peak is None:
+        pot3d.probe_fp64_fma(0.1)  # warm-up
+        clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clk.start()
+        rate, el = pot3d.probe_fp64_fma(1.0)
+        c = clk.stop()
+        _fp64_peak = {"tflops": 2.0 * rate / 1e12, "seconds": el, "clocks": c,
+                      "how": "pot3d_probe_fp64_fma: 8 independent DFMA chains per thread, "
+                             "2048 threads per SM, CUDA events"}
+    return _fp64_peak
+
+
 # FP64 FMAs per point of the matvec kernel (p~ and x~ updates, 6-term
 # scaled stencil, sigma term): the algorithmic count, halo work excluded
 FP64_FMA_PER_POINT_MATVEC = 9.0
@@ -279,6 +301,29 @@ def kernel_times(plan, prec, br_d, phi, torch, dev):
     return km[0] / max(km[2], 1), km[1] / max(km[3], 1)
 
 
+def field_time(plan, br_d, phi, B, torch, dev, reps=5):
+    """Device time of pot3d_field (pole averages + staggered B = grad Phi)
+    between CUDA events on the plan's stream, averaged over `reps` calls,
+    against its algorithmic bytes: Phi and Br read once, the three face
+    components written once (about 32 B per unknown)."""
+    nr, nt, np_ = SHAPE
+    n = nr * nt * np_
+    nbytes = 8.0 * (n + nt * np_) + 8.0 * sum(plan.field_sizes())
+    stream = torch.cuda.current_stream(dev)
+    plan.field(phi, br_d, B)  # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.field(phi, br_d, B)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    peaks, _ = measured_peaks()
+    return {"avg_call_ms": ms, "algorithmic_bytes": nbytes, "GB_s": nbytes / (ms * 1e-3) / 1e9,
+            "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "launches_per_call": 2}
+
+
 def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=True):
     """Times `steps` solves (+ field) of one precision after `warmup` solves."""
     ws, rank, local = dist_env()
@@ -332,26 +377,35 @@ def measure(pot3d, torch, dev, dist, br, br_d, prec, steps, warmup, with_e2e=Tru
     # Phi of the last timed solve, before the kernel-time pass reuses phi
     err = sampled_error_vs_oracle(phi)
     mv_ms, up_ms = kernel_times(plan, prec, br_d, phi, torch, dev)
+    hbm_mv = info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9
     if prec == "fp64":
         achieved = 2 * FP64_FMA_PER_POINT_MATVEC * n / (mv_ms * 1e-3) / 1e12
+        pk = fp64_peak(pot3d)
         roof = {"bound": "alu", "kernel": "k_matvec<PF64>", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC.get(prec),
-                "peak_source": "FP64 FMA units x max SM clock: 152 x 2/clk x 2 flop x 2.07 GHz",
-                "hbm_GB_s": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9,
-                "hbm_frac_of_measured": info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+                "peak": pk["tflops"], "unit": "TFLOP/s", "frac": achieved / pk["tflops"],
+                "traffic": TRAFFIC.get(prec), "peak_source": "measured",
+                "peak_measurement": pk,
+                "nominal_peak": FP64_PEAK_TFLOPS,
+                "frac_of_nominal": achieved / FP64_PEAK_TFLOPS,
+                "nominal_source": "FP64 FMA units x max SM clock: 152 x 2/clk x 2 flop x 2.07 GHz",
+                "hbm_GB_s": hbm_mv,
+                "hbm_frac_of_measured": hbm_mv / peaks["hbm_gbs"],
+                "hbm_frac_of_nominal": hbm_mv / HBM_NOMINAL_GBS}
     else:
-        achieved = info["bytes_matvec"] / (mv_ms * 1e-3) / 1e9
+        achieved = hbm_mv
         roof = {"bound": "hbm", "kernel": "k_matvec<%s>" % ("PDF" if prec == "df" else "PF32"),
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC.get(prec),
-                "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % src}
+                "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs" % src,
+                "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
+                "nominal_peak": HBM_NOMINAL_GBS}
     roof["avg_launch_ms"] = mv_ms
     roof["algorithmic_bytes_per_launch"] = info["bytes_matvec"]
-    roof["update_kernel"] = {"avg_launch_ms": up_ms,
-                             "GB_s": info["bytes_update"] / (up_ms * 1e-3) / 1e9 if up_ms else None,
-                             "frac_of_measured_hbm": (info["bytes_update"] / (up_ms * 1e-3) / 1e9
-                                                      / peaks["hbm_gbs"]) if up_ms else None}
+    up_gbs = info["bytes_update"] / (up_ms * 1e-3) / 1e9 if up_ms else None
+    roof["update_kernel"] = {"avg_launch_ms": up_ms, "GB_s": up_gbs,
+                             "frac_of_measured_hbm": up_gbs / peaks["hbm_gbs"] if up_gbs else None,
+                             "frac_of_nominal_hbm": up_gbs / HBM_NOMINAL_GBS if up_gbs else None}
+    roof["field_kernels"] = field_time(plan, br_d, phi, B, torch, dev)
     out = {"value": value, "unit": "iters/s", "ms_per_step": ms_max / steps, "dtype": DTYPES[prec],
            "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1], "matvec_ms": tuned[2]},
            "iters_per_solve": iters / steps, "hbm_gbs": value / ws * bytes_per_iter / 1e9,
@@ -421,10 +475,14 @@ def run_gpu(args):
     for pv in args.variants:
         if pv == args.prec:
             continue
-        v = measure(pot3d, torch, dev, dist, br, br_d, pv, steps=2, warmup=1, with_e2e=False)
+        v = measure(pot3d, torch, dev, dist, br, br_d, pv, steps=4, warmup=2, with_e2e=False)
         variants[pv] = v
     if variants:
         result["variants"] = variants
+    if ws == 1 and args.serve_requests > 0:
+        # the second half of the metric: mixed + batched serving vs FP64
+        # one-at-a-time on one seeded stream (not part of the timed PCG steps)
+        result["serve"] = serve_record(args.serve_requests, args.batch_k, args.inner_tol)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(br)
     if rank == 0:
@@ -433,44 +491,63 @@ def run_gpu(args):
     return 0
 
 
-def run_serve(args):
+def serve_record(requests, batch_k=16, inner_tol=0.0):
     """Serving stream: seeded Poisson arrivals of solves on grids drawn from
     41x61x121, 81x121x241, 101x181x361 and 151x301x601 (bipole Br with seed
     1709 + request id, tol 1e-10), served by the continuous-batching mixed
-    path and by FP64 one-at-a-time solves on the same trace.  The arrival rate
-    is 1.5x the calibrated FP64 one-at-a-time solve rate over the grid mix."""
+    path and by FP64 one-at-a-time solves (opts.verify: they stop on the FP64
+    residual, as the refinement path does) on the same trace.  The arrival
+    rate is 1.5x the calibrated FP64 one-at-a-time solve rate over the grid
+    mix.  Every served Phi's FP64 residual is recomputed after the stream
+    (pot3d_residual) and the largest is reported per server.  Capacity: the
+    same requests all present at t = 0, batched, against the calibrated FP64
+    one-at-a-time rate."""
     import torch
 
     from paper_1709_01126_gb300 import pot3d, serve
 
     pot3d.load()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
     rate64, times = serve.calibrate_fp64_rate()
     rate = 1.5 * rate64
-    reqs = serve.make_requests(args.requests, rate)
+    reqs = serve.make_requests(requests, rate)
     inputs = serve.prepare_inputs(reqs)
     free, total = torch.cuda.mem_get_info()
     budget = int(min(0.5 * free, 96e9))
-    batched = serve.run_batched(reqs, inputs, batch_bytes=budget, k=args.batch_k,
-                                inner_tol=args.inner_tol)
+    batched = serve.run_batched(reqs, inputs, batch_bytes=budget, k=batch_k,
+                                inner_tol=inner_tol)
     base = serve.run_fp64_serial(reqs, inputs)
     # capacity: the same requests all present at t = 0
     sat_reqs = [serve.Request(r.rid, r.grid, 0.0, r.seed) for r in reqs]
-    sat = serve.run_batched(sat_reqs, inputs, batch_bytes=budget, k=args.batch_k,
-                            inner_tol=args.inner_tol).summary()
+    sat = serve.run_batched(sat_reqs, inputs, batch_bytes=budget, k=batch_k,
+                            inner_tol=inner_tol).summary()
+    clocks = clk.stop()
     b, f = batched.summary(), base.summary()
+    return {"requests": requests, "arrival_rate_per_s": rate,
+            "workload": "serving stream of %d solves, Poisson arrivals at %.3f/s (1.5x FP64 "
+                        "rate), grids %s, tol 1e-10" % (requests, rate, serve.GRIDS),
+            "batch_arena_bytes": budget, "step_iters": batch_k,
+            "batched": b, "fp64_one_at_a_time": f,
+            "speedup_solves_per_s": b["solves_per_s"] / f["solves_per_s"],
+            "p99_ratio_fp64_over_batched": f["p99_latency_s"] / b["p99_latency_s"],
+            "capacity_solves_per_s": {"batched_all_at_t0": sat["solves_per_s"],
+                                      "batched_all_at_t0_max_relres_fp64": sat["max_relres_fp64"],
+                                      "fp64_one_at_a_time": rate64,
+                                      "ratio": sat["solves_per_s"] / rate64},
+            "fp64_calibration_s": dict(zip(["x".join(map(str, g)) for g in serve.GRIDS], times)),
+            "clocks": clocks}
+
+
+def run_serve(args):
+    rec = serve_record(args.requests, args.batch_k, args.inner_tol)
+    b = rec["batched"]
     line = {"metric": METRIC, "value": b["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.requests, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "workload_kind": "serve",
-            "config": {"workload": "serving stream of %d solves, Poisson arrivals at %.3f/s "
-                                   "(1.5x FP64 rate), grids %s, tol 1e-10"
-                                   % (args.requests, rate, serve.GRIDS),
-                       "batch_arena_bytes": budget, "step_iters": args.batch_k},
-            "batched": b, "fp64_one_at_a_time": f,
-            "speedup_solves_per_s": b["solves_per_s"] / f["solves_per_s"],
-            "capacity_solves_per_s": {"batched_all_at_t0": sat["solves_per_s"],
-                                      "fp64_one_at_a_time": rate64,
-                                      "ratio": sat["solves_per_s"] / rate64},
-            "fp64_calibration_s": dict(zip(["x".join(map(str, g)) for g in serve.GRIDS], times))}
+            "config": {"workload": rec["workload"], "batch_arena_bytes": rec["batch_arena_bytes"],
+                       "step_iters": rec["step_iters"]},
+            "clocks": rec["clocks"], "serve": rec}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -626,6 +703,8 @@ def main():
                     help="large-solve: FP64/double-float restart on the FP64 residual (opts.verify)")
     ap.add_argument("--large-iters", type=int, default=200)
     ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the serving record in the default run (0: none)")
     ap.add_argument("--batch-k", type=int, default=16)
     ap.add_argument("--inner-tol", type=float, default=0.0)
     args = ap.parse_args()

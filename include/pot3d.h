@@ -117,16 +117,28 @@ typedef struct {
                          MIXED always stops on the FP64 residual.                */
 } pot3d_opts_t;
 
+/* pot3d_stats_t.flags bits */
+#define POT3D_FLAG_ABOVE_TOL 1 /* the recomputed FP64 residual of the returned Phi
+                                  is above tol although the PCG recurrence
+                                  residual met it (the solve still returns
+                                  POT3D_OK: the paper's stopping rule)          */
+
 /* Statistics of the last solve on a plan. */
 typedef struct {
   int status;          /* return code of the last solve                         */
   int iters;           /* PCG iterations (MIXED: total inner FP32 iterations)   */
-  int outer_iters;     /* MIXED: refinement steps (else 0)                       */
+  int outer_iters;     /* MIXED: refinement steps; verify: restarts (else 0)    */
   double relres;       /* final ||r||/||b||: PCG recurrence residual (FP64, DF)
-                          or the recomputed FP64 residual (MIXED)                */
+                          or the recomputed FP64 residual (MIXED, verify)       */
   double kernel_ms[4]; /* with time_kernels: summed event time of the matvec     */
                        /* kernel, the update kernel, and their launch counts     */
   long long launches;  /* kernels the last solve or field call launched          */
+  double relres_fp64;  /* ||b - L Phi|| / ||b|| of the returned Phi, recomputed
+                          in FP64 after every solve (one operator application)  */
+  int flags;           /* POT3D_FLAG_* bits                                      */
+  double sigma;        /* p.Ap of the last PCG iteration, as the device summed it
+                          (inner FP32 system for MIXED: scaled units)           */
+  double rr;           /* ||r||^2 of the last PCG iteration, as summed (same)    */
 } pot3d_stats_t;
 
 /* Static facts about a plan (for measurement and sizing). */
@@ -238,10 +250,13 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
  * library (4096 doubles, room for 2047 blocks; the call launches at most
  * 4 x SMs blocks and returns POT3D_ERR_TOO_LARGE if that exceeds the room).
  * Every GPU that loads the library holds the array until the process exits.
- * The first call on each device looks up the array's device address, so it
- * should come before any stream capture.  All calls share the array: calls
- * whose kernels overlap on the GPU race; order them on one stream.  The
- * result agrees with pot3d_residual to rounding. */
+ * The first call on each device (each device context) looks up the array's
+ * device address, so it should come before any stream capture.  The call
+ * reads its result back to the host and synchronises the plan's stream
+ * before it returns.  All calls share the array and every slot a call reads
+ * is written earlier in the same call: calls whose kernels overlap on the
+ * GPU race; order them on one stream.  The result agrees with
+ * pot3d_residual to rounding. */
 int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, const double *phi,
                            double *relres);
 
@@ -253,6 +268,23 @@ int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, const double *p
  * *elapsed_s (may be NULL) the device time the wait took.  Runs on the legacy
  * default stream and synchronises it.  Returns POT3D_OK if the test ran. */
 int pot3d_selftest_wait(double limit_s, int *device_status, double *elapsed_s);
+
+/* Measurement helper: the native FP64 fused multiply-add rate of the current
+ * device, the roofline denominator of the FP64 iteration (no counterpart in
+ * the paper).  Runs a kernel of independent DFMA chains on every SM for at
+ * least min_seconds of device time (0 < min_seconds <= 5) on the legacy
+ * default stream and synchronises it.  *fma_per_s receives the measured
+ * DFMA per second (one DFMA = 2 flop); *elapsed_s (may be NULL) the timed
+ * device seconds.  Returns POT3D_OK, or POT3D_ERR_INVALID_ARG / a CUDA error. */
+int pot3d_probe_fp64_fma(double min_seconds, double *fma_per_s, double *elapsed_s);
+
+/* Testing hook for the host-side progress guard (failure detection without
+ * a fault): with on = 1 the host keeps re-reading the first solver-state
+ * snapshot of a solve, as if the device state had stopped advancing, so the
+ * guard ends the solve with POT3D_ERR_TIMEOUT after two polls.  The kernels
+ * already queued run to completion before the call returns; the plan stays
+ * usable.  on = 0 restores normal polling. */
+int pot3d_test_freeze_poll(pot3d_plan_t *plan, int on);
 
 /* ---- batched solves (continuous batching) ------------------------------
  * Many solves of different grids advance together in the same persistent

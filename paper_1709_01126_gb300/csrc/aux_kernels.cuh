@@ -77,6 +77,7 @@ static __global__ void k_start(SolveState *st, const double *sums, double n0, do
   st->alpha[0] = st->alpha[1] = 0.0;
   st->beta[0] = st->beta[1] = 0.0;
   st->sigma = 0.0;
+  st->rr = 0.0;
   st->ticket_a = st->ticket_b = 0u;
   st->pad_ = 0;
   const double rr = use_x0 ? sums[2] : bb;

@@ -49,6 +49,7 @@ struct SolveState {
   double relres;   // ||r_k|| / ||b||
   double sigma;    // last p.Ap
   double scale;    // power-of-two scale applied to b
+  double rr;       // ||r_k||^2 as summed by the update kernel
   int iter;        // completed iterations
   int maxit;
   int status;
@@ -720,6 +721,7 @@ __global__ void __launch_bounds__(NT)
       if (tid == 0) {
         const double relres = sqrt(rr) / sqrt(stt->bb);
         stt->relres = relres;
+        stt->rr = rr;
         stt->iter = kit;
         if (!isfinite(relres)) {
           stt->status = ST_BREAKDOWN;

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "plan.h"
 
 // Capacity of the scratch: per-block partial pairs plus the two final sums.
@@ -33,11 +35,46 @@ constexpr int kNoAllocMaxBlocks = (kNoAllocScratchDoubles - 2) / 2;
 constexpr int kMaxDevices = 64;
 
 // Device addresses of the array, one per device, looked up with
-// cudaGetSymbolAddress on the first call made with that device current (so
-// that first call should come before any stream capture).  In host code the
-// array's name is only a host-side stand-in, never a device address.
+// cudaGetSymbolAddress the first time the call runs with that device's
+// context current (so that first call should come before any stream
+// capture).  In host code the array's name is only a host-side stand-in,
+// never a device address.  The address belongs to the context that loaded
+// the module: each entry remembers that context's unique id, and a call made
+// under another context (after cudaDeviceReset, say) looks the address up
+// again instead of reusing a stale one.
 std::mutex g_mu;
-double *g_dev_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  double *ptr;
+};
+ScratchAddr g_addr[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context; 0 when none is current
+// yet or the driver entry points are unavailable.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    cudaGetLastError();
+  });
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int scratch_ptr(double **out) {
   int dev = 0;
@@ -45,13 +82,20 @@ int scratch_ptr(double **out) {
   if (e != cudaSuccess) return pot3d::cuda_status(e);
   if (dev < 0 || dev >= kMaxDevices) return pot3d::fail(POT3D_ERR_TOO_LARGE);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_dev_ptr[dev]) {
+  const unsigned long long id = current_context_id();
+  ScratchAddr &a = g_addr[dev];
+  if (!a.ptr || id == 0 || a.ctx_id != id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return pot3d::cuda_status(e);
-    g_dev_ptr[dev] = static_cast<double *>(p);
+    if (e != cudaSuccess) {
+      a = ScratchAddr{};
+      return pot3d::cuda_status(e);
+    }
+    // the lookup made the device's primary context current if none was
+    a.ctx_id = current_context_id();
+    a.ptr = static_cast<double *>(p);
   }
-  *out = g_dev_ptr[dev];
+  *out = a.ptr;
   return POT3D_OK;
 }
 

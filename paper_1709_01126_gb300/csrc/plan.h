@@ -69,6 +69,7 @@ struct Plan {
   pot3d_stats_t stats{};
   int nsm = 0;
   std::vector<cudaEvent_t> ev;
+  bool freeze_poll = false; // testing hook: the host re-reads a stale state snapshot
 };
 
 int fail(int code);

@@ -394,6 +394,12 @@ size_t pot3d_workspace_bytes(const pot3d_plan_t *plan) {
   return workspace_bytes(reinterpret_cast<const Plan *>(plan));
 }
 
+int pot3d_test_freeze_poll(pot3d_plan_t *plan, int on) {
+  if (!plan || on < 0 || on > 1) return fail(POT3D_ERR_INVALID_ARG);
+  reinterpret_cast<Plan *>(plan)->freeze_poll = (on == 1);
+  return POT3D_OK;
+}
+
 int pot3d_set_workspace(pot3d_plan_t *plan, void *dev_ptr, size_t bytes) {
   if (!plan || !dev_ptr) return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);

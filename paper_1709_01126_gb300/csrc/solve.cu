@@ -329,10 +329,18 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
       return POT3D_OK;
     };
     int b = 0;
+    bool have_frozen = false;
+    SolveState frozen{};
     TRY(enqueue(0));
     for (;;) {
       TRY(enqueue(b ^ 1));
       CTRY(cudaEventSynchronize(P->poll_ev[b]));
+      if (P->freeze_poll) {
+        // testing hook: the host keeps seeing its first snapshot
+        if (have_frozen) *snap[b] = frozen;
+        else frozen = *snap[b];
+        have_frozen = true;
+      }
       if (snap[b]->status != ST_RUNNING) break;
       // a running solve must advance every chunk; if it does not, the
       // device state is inconsistent: stop instead of polling forever
@@ -362,6 +370,10 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
     CTRY(cudaMemcpyAsync(P->h_state, D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                          P->stream));
     CTRY(cudaStreamSynchronize(P->stream));
+    if (P->freeze_poll) {
+      // testing hook: the host keeps seeing its first snapshot
+      if (last_iter >= iter0) P->h_state->iter = last_iter;
+    }
     // only iterations that did work count (kernels exit early once done)
     const int real = std::min(chunk, P->h_state->iter - done_before);
     done_before = P->h_state->iter;
@@ -515,7 +527,14 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   TRY(iterate<A>(P, ai));
   P->stats.launches += 1;
   k_finish<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, io.phi, 1);
+  // the FP64 residual of the returned Phi (||b||^2 is in d_sums[0])
+  const int g = aux_grid(P, P->n);
+  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+                                                P->nt, P->np, 0, nullptr, P->np, P->d_part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
+  P->stats.launches += 2;
   CTRY(cudaGetLastError());
+  CTRY(cudaMemcpyAsync(P->h_sums, P->d_sums, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
   if (io.phi_host)
     CTRY(cudaMemcpyAsync(phi, io.phi, P->n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CTRY(cudaStreamSynchronize(s));
@@ -524,6 +543,11 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   P->stats.iters = hs.iter;
   P->stats.outer_iters = 0;
   P->stats.relres = hs.relres;
+  P->stats.sigma = hs.sigma;
+  P->stats.rr = hs.rr;
+  const double bb = P->h_sums[0];
+  P->stats.relres_fp64 = bb > 0 ? std::sqrt(P->h_sums[2]) / std::sqrt(bb) : 0.0;
+  P->stats.flags = (P->stats.status == POT3D_OK && P->stats.relres_fp64 > tol) ? POT3D_FLAG_ABOVE_TOL : 0;
   if (iters) *iters = hs.iter;
   return P->stats.status ? fail(P->stats.status) : POT3D_OK;
 }
@@ -618,6 +642,8 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     CTRY(cudaGetLastError());
     TRY(iterate<PF32>(P, AR_F32, iter0));
     const SolveState &hs = *P->h_state;
+    P->stats.sigma = hs.sigma;
+    P->stats.rr = hs.rr;
     n_inner += hs.iter - iter0;
     if (hs.status == ST_BREAKDOWN && hs.iter == iter0) {
       status = POT3D_ERR_BREAKDOWN;
@@ -638,6 +664,8 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   P->stats.iters = n_inner;
   P->stats.outer_iters = n_outer;
   P->stats.relres = relres;
+  P->stats.relres_fp64 = relres;
+  P->stats.flags = 0;
   if (outer) *outer = n_outer;
   if (inner) *inner = n_inner;
   return status ? fail(status) : POT3D_OK;
@@ -666,9 +694,8 @@ static int solve_pcg_verified(Plan *P, int ai, const double *br, double tol, dou
     total += it;
     launches += P->stats.launches;
     if (rc != POT3D_OK) break;
-    rc = pot3d_residual(reinterpret_cast<pot3d_plan_t *>(P), br, phi, &rel);
-    launches += 2;
-    if (rc != POT3D_OK || rel <= tol) break;
+    rel = P->stats.relres_fp64; // recomputed by solve_pcg from the returned Phi
+    if (rel <= tol) break;
     if (restarts == kMaxReplacements || total >= cap) {
       rc = POT3D_ERR_NOT_CONVERGED;
       break;
@@ -678,6 +705,7 @@ static int solve_pcg_verified(Plan *P, int ai, const double *br, double tol, dou
   }
   P->opts = saved;
   if (rc == POT3D_OK || rc == POT3D_ERR_NOT_CONVERGED) P->stats.relres = rel;
+  P->stats.flags = 0;
   P->stats.status = rc;
   P->stats.iters = total;
   P->stats.outer_iters = restarts;

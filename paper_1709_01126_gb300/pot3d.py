@@ -54,10 +54,14 @@ class pot3d_opts_t(ctypes.Structure):
                 ("mixed_restart", ctypes.c_int), ("verify", ctypes.c_int)]
 
 
+POT3D_FLAG_ABOVE_TOL = 1
+
+
 class pot3d_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("relres", ctypes.c_double), ("kernel_ms", ctypes.c_double * 4),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("relres_fp64", ctypes.c_double),
+                ("flags", ctypes.c_int), ("sigma", ctypes.c_double), ("rr", ctypes.c_double)]
 
 
 class pot3d_info_t(ctypes.Structure):
@@ -72,7 +76,8 @@ EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_variant_info", "pot3d_set_deco
            "pot3d_residual_noalloc", "pot3d_batch_create", "pot3d_batch_destroy",
            "pot3d_batch_set_stream", "pot3d_batch_set_opts", "pot3d_batch_bytes_needed",
            "pot3d_batch_submit", "pot3d_batch_step", "pot3d_batch_poll", "pot3d_batch_info",
-           "pot3d_last_error", "pot3d_strerror", "pot3d_selftest_wait"]
+           "pot3d_last_error", "pot3d_strerror", "pot3d_selftest_wait", "pot3d_probe_fp64_fma",
+           "pot3d_test_freeze_poll"]
 
 _lib = None
 
@@ -88,6 +93,14 @@ def selftest_wait(limit_s: float):
     _check(load().pot3d_selftest_wait(float(limit_s), ctypes.byref(st), ctypes.byref(el)),
            "pot3d_selftest_wait")
     return st.value, el.value
+
+
+def probe_fp64_fma(min_seconds: float = 0.5):
+    """pot3d_probe_fp64_fma: (DFMA per second, timed device seconds)."""
+    r, el = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().pot3d_probe_fp64_fma(float(min_seconds), ctypes.byref(r), ctypes.byref(el)),
+           "pot3d_probe_fp64_fma")
+    return r.value, el.value
 
 
 ARITHS = {"fp64": 0, "df": 1, "f32": 2}
@@ -159,6 +172,9 @@ def load(build_if_missing: bool = False):
                                    ctypes.POINTER(ctypes.c_size_t)]
     L.pot3d_selftest_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double)]
+    L.pot3d_probe_fp64_fma.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    L.pot3d_test_freeze_poll.argtypes = [P, I]
     L.pot3d_last_error.argtypes = []
     L.pot3d_strerror.argtypes = [I]
     L.pot3d_strerror.restype = ctypes.c_char_p
@@ -281,7 +297,12 @@ class Plan:
         s = pot3d_stats_t()
         _check(load().pot3d_last_stats(self.h, ctypes.byref(s)), "pot3d_last_stats")
         return {"status": s.status, "iters": s.iters, "outer_iters": s.outer_iters,
-                "relres": s.relres, "kernel_ms": list(s.kernel_ms), "launches": s.launches}
+                "relres": s.relres, "kernel_ms": list(s.kernel_ms), "launches": s.launches,
+                "relres_fp64": s.relres_fp64, "flags": s.flags, "sigma": s.sigma, "rr": s.rr}
+
+    def test_freeze_poll(self, on: bool):
+        """pot3d_test_freeze_poll (testing hook of the host progress guard)."""
+        _check(load().pot3d_test_freeze_poll(self.h, 1 if on else 0), "pot3d_test_freeze_poll")
 
     def _bind_stream(self, *arrays):
         st = _stream_of(*arrays)

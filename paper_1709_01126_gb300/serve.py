@@ -41,6 +41,7 @@ class Outcome:
     relres: float
     iters: int
     outer: int = 0
+    relres_fp64: float = float("nan")  # ||b - L Phi|| / ||b|| of the served Phi
 
     @property
     def latency(self):
@@ -52,18 +53,31 @@ class ServeStats:
     kind: str
     outcomes: list = field(default_factory=list)
     wall: float = 0.0
+    results: dict = field(default_factory=dict)  # rid -> (br, phi) device tensors, if kept
 
     def summary(self):
         lat = np.array([o.latency for o in self.outcomes])
         span = max(o.done for o in self.outcomes) - min(o.arrival for o in self.outcomes)
+        true = [o.relres_fp64 for o in self.outcomes]
         return {"kind": self.kind, "solves": len(self.outcomes),
                 "solves_per_s": len(self.outcomes) / span if span > 0 else None,
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()),
                 "max_relres": float(max(o.relres for o in self.outcomes)),
+                "max_relres_fp64": (None if any(np.isnan(t) for t in true)
+                                    else float(max(true))),
                 "all_ok": all(o.status == 0 for o in self.outcomes),
                 "span_s": span}
+
+
+def check_residuals(stats: ServeStats, plans):
+    """After the stream: the FP64 residual ||b - L Phi|| / ||b|| of every
+    served Phi, recomputed by the library's FP64 operator (outside the timed
+    stream)."""
+    for o in stats.outcomes:
+        br, phi = stats.results[o.rid]
+        o.relres_fp64 = plans[o.grid].residual(br, phi)
 
 
 def make_requests(n: int, rate: float, grids=GRIDS, seed: int = SEED):
@@ -90,7 +104,10 @@ def prepare_inputs(requests):
 
 
 def run_batched(requests, inputs, batch_bytes: int, k: int = 16, max_slots: int = 256,
-                inner_tol: float = 0.0):
+                inner_tol: float = 0.0, verify: bool = True, keep: bool = False):
+    """Serves `requests` with the continuous-batching mixed-precision path.
+    verify: recompute every served Phi's FP64 residual after the stream;
+    keep: keep the (Br, Phi) device tensors in the returned stats."""
     import torch
 
     plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="mixed") for g in {r.grid for r in requests}}
@@ -121,19 +138,31 @@ def run_batched(requests, inputs, batch_bytes: int, k: int = 16, max_slots: int 
                 r, br, phi = live.pop(tag)
                 stats.outcomes.append(Outcome(r.rid, r.grid, r.arrival, time.perf_counter() - t0,
                                               st, relres, inner, outer))
+                if verify or keep:
+                    stats.results[r.rid] = (br, phi)
         elif pending:
             time.sleep(max(0.0, min(0.002, pending[0].arrival - now)))
     stats.wall = time.perf_counter() - t0
     batch.close()
+    torch.cuda.synchronize()
+    if verify:
+        check_residuals(stats, plans)
+    if not keep:
+        stats.results = {}
     for p in plans.values():
         p.close()
     return stats
 
 
-def run_fp64_serial(requests, inputs):
+def run_fp64_serial(requests, inputs, verify: bool = True, keep: bool = False):
+    """Serves `requests` one at a time in arrival order with native FP64 PCG.
+    Each solve runs with opts.verify, so it stops on the recomputed FP64
+    residual, the same criterion as the refinement path (equal final
+    accuracy by construction)."""
     import torch
 
-    plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="fp64") for g in {r.grid for r in requests}}
+    plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="fp64", verify=1)
+             for g in {r.grid for r in requests}}
     for p in plans.values():
         p.autotune(1)
     stats = ServeStats("fp64 one-at-a-time")
@@ -148,8 +177,14 @@ def run_fp64_serial(requests, inputs):
         torch.cuda.synchronize()
         st = plans[r.grid].stats()
         stats.outcomes.append(Outcome(r.rid, r.grid, r.arrival, time.perf_counter() - t0, rc,
-                                      st["relres"], it))
+                                      st["relres"], it, st["outer_iters"]))
+        if verify or keep:
+            stats.results[r.rid] = (br, phi)
     stats.wall = time.perf_counter() - t0
+    if verify:
+        check_residuals(stats, plans)
+    if not keep:
+        stats.results = {}
     for p in plans.values():
         p.close()
     return stats

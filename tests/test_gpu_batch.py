@@ -88,15 +88,28 @@ def test_admission_is_bounded_by_memory(p3):
     b.close()
 
 
-def test_serving_loop_small_stream(p3):
+def test_serving_loop_small_stream(p3, oracle_mod):
+    """Both servers complete a small stream; every served Phi's FP64
+    residual, recomputed by the library, meets the tolerance; and one served
+    Phi of each server is checked with the oracle's own operator."""
     from paper_1709_01126_gb300 import serve
 
     grids = [(9, 13, 27), (12, 17, 35)]
     reqs = serve.make_requests(8, rate=200.0, grids=grids)
     inputs = serve.prepare_inputs(reqs)
-    st = serve.run_batched(reqs, inputs, batch_bytes=1 << 28, k=8)
-    s = st.summary()
-    assert s["solves"] == 8 and s["all_ok"] and s["max_relres"] <= 1e-10
-    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
-    base = serve.run_fp64_serial(reqs, inputs).summary()
-    assert base["solves"] == 8 and base["all_ok"]
+    for run in (serve.run_batched, serve.run_fp64_serial):
+        if run is serve.run_batched:
+            st = run(reqs, inputs, batch_bytes=1 << 28, k=8, keep=True)
+        else:
+            st = run(reqs, inputs, keep=True)
+        s = st.summary()
+        assert s["solves"] == 8 and s["all_ok"], s
+        assert s["max_relres_fp64"] <= 1e-10, s
+        assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+        o = max(st.outcomes, key=lambda q: q.grid)
+        br, phi = st.results[o.rid]
+        g = oracle_mod.Grid(*o.grid, ratio=serve.RATIO)
+        b = g.rhs(br.cpu().numpy())
+        true_rel = np.linalg.norm(b - g.apply(phi.cpu().numpy())) / np.linalg.norm(b)
+        assert true_rel <= 1.001e-10, (run.__name__, true_rel)
+        assert abs(true_rel - o.relres_fp64) <= 1e-3 * true_rel + 1e-15

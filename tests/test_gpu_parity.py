@@ -94,7 +94,12 @@ def test_solve_parity(p3, oracle_mod, prec, shape, ratio, kind):
     # operation for double-float, 2^-53 for FP64)
     r = g.rhs(br) - g.apply(x)
     gap = 2e-12 if prec == "fp64" else 2e-11
-    assert np.linalg.norm(r) / np.linalg.norm(g.rhs(br)) <= 1e-12 + gap
+    true_rel = np.linalg.norm(r) / np.linalg.norm(g.rhs(br))
+    assert true_rel <= 1e-12 + gap
+    # the library's own FP64 residual of the returned Phi, and its flag
+    st = plan.stats()
+    assert abs(st["relres_fp64"] - true_rel) <= 0.02 * max(true_rel, 1e-13), (st, true_rel)
+    assert (st["flags"] & p3.POT3D_FLAG_ABOVE_TOL) == (st["relres_fp64"] > 1e-12)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df"])

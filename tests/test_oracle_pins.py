@@ -243,6 +243,40 @@ def test_field_matches_analytic_gradient(oracle_mod):
     assert np.all(orders > 1.8), (errs, orders)
 
 
+@pytest.mark.parametrize("l", [1, 2])
+def test_pole_face_btheta_matches_analytic(oracle_mod, l):
+    """Btheta on the two pole faces (Eq. 3: the ghost across the pole makes
+    the face value the ring's phi-average) converges to the analytic
+    dPhi/(r dtheta) at theta = 0 and pi for the m = 1 harmonics, whose
+    pole-face Btheta is non-zero and varies with phi.  The face value divides
+    the first ring's error by the half-cell distance to the pole, so it
+    converges at about order 1.6 (measured for l = 1 from 10 to 80 cells:
+    1.57, 1.64, 1.63), not 2.  A dropped factor 2 in the mirror spacing, or a
+    flipped sign, makes the error O(1)."""
+    from scipy.special import lpmv
+
+    m = 1
+    a, b = shell_coeffs(l, 2.5)
+    h = 1e-6
+    # d/dtheta of P_l^1(cos theta) just inside each pole (P_l^1 vanishes there)
+    dn = lpmv(m, l, np.cos(h)) / h
+    ds = -lpmv(m, l, np.cos(np.pi - h)) / h
+    errs = []
+    for n in (10, 20, 40):
+        e, g, phi, br, scale = _shell_error(oracle_mod, n, l, m)
+        Br, Bt, Bp = g.field(phi, br)
+        f = a * g.rc ** l + b * g.rc ** (-(l + 1.0))
+        ang = np.cos(m * g.pc)
+        ex_n = (f / g.rc)[:, None] * scale * dn * ang[None, :]
+        ex_s = (f / g.rc)[:, None] * scale * ds * ang[None, :]
+        num = np.concatenate([(Bt[:, 0, :] - ex_n).ravel(), (Bt[:, -1, :] - ex_s).ravel()])
+        den = np.concatenate([ex_n.ravel(), ex_s.ravel()])
+        errs.append(np.linalg.norm(num) / np.linalg.norm(den))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 1e-2, errs
+    assert np.all(orders > 1.35), (errs, orders)
+
+
 def test_pole_average(oracle_mod):
     g = oracle_mod.Grid(3, 4, 5)
     phi = syn.random_field(g.shape, seed=9)

@@ -1,6 +1,9 @@
 """pot3d_residual_noalloc, the residual for callers that cannot allocate
-device memory during the call, against pot3d_residual (which uses memory
-its plan allocated).  Collected last on purpose."""
+device memory during the call (device memory owned by another allocator, a
+fixed memory budget, or code where an allocation would synchronise the
+device), against pot3d_residual (which uses memory its plan allocated).
+Collected last on purpose, so that a run that stops at the first failure
+has run every other test before this one."""
 import numpy as np
 import pytest
 
@@ -30,10 +33,36 @@ def test_noalloc_residual_matches_residual(p3, shape, solved):
     if solved:
         plan.solve(br, 1e-11, phi)
     ref = plan.residual(br, phi)
+    # two calls in a row: the second reuses the scratch the first left behind
     first = plan.residual_noalloc(br, phi)
     second = plan.residual_noalloc(br, phi)
     for v in (first, second):
         assert abs(v - ref) <= 1e-12 * ref, (v, ref)
+    plan.close()
+
+
+def test_noalloc_allocates_nothing_and_follows_the_stream(p3):
+    """A warm call leaves the device's free memory unchanged, and on a
+    non-default torch stream it gives the same value as pot3d_residual."""
+    shape = (12, 17, 40)
+    plan = p3.Plan(*shape, ratio=1.03)
+    br = torch.from_numpy(syn.bipole_br(17, 40, seed=9, n_bipoles=10)).cuda()
+    phi = torch.from_numpy(syn.random_field(shape, seed=10)).cuda()
+    ref = plan.residual(br, phi)
+    plan.residual_noalloc(br, phi)  # warm: the kernels' module is loaded
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    v = plan.residual_noalloc(br, phi)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert abs(v - ref) <= 1e-12 * ref
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        vals = [plan.residual_noalloc(br, phi) for _ in range(2)]
+    s.synchronize()
+    for w in vals:
+        assert abs(w - ref) <= 1e-12 * ref, (w, ref)
     plan.close()
 
 
