@@ -6,8 +6,9 @@ package.  It shares no code with the GPU library: the C source next to this
 file (``pot3d_oracle.c``) has its own mesh, coefficient, operator, PCG and
 field code, written step by step from the paper:
 
-- Sec. 2.1, Eqs. 1-3: Laplace equation, inner Br condition, source surface,
-  periodic phi and the polar average.
+- Sec. 2.1, Eqs. 1-3: Laplace equation, inner Br condition, source surface
+  (or its alternative, the closed wall Br = 0), periodic phi and the polar
+  average.
 - Sec. 2.2 (finite-difference stencil) and Eq. 4: the 7-point operator, in
   its symmetric volume-weighted form with the r^2 metric factors restored.
 - Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1).
@@ -64,6 +65,10 @@ def _load():
             lib.orc_field.argtypes = [i, i, i, _dp, _dp, _dp, _dp, _dp]
             lib.orc_csr.argtypes = [i, i, i, _dp, _dp, _lp, _lp, _dp]
             lib.orc_csr.restype = ctypes.c_long
+            lib.orc_set_outer.argtypes = [i]
+            lib.orc_balance_br.argtypes = [i, i, i, _dp, _dp, _dp, _dp]
+            lib.orc_remove_mean.argtypes = [ctypes.c_long, _dp]
+            lib.orc_remove_mean.restype = None
             lib.orc_set_threads.argtypes = [i]
             lib.orc_get_threads.restype = i
             _lib = lib
@@ -83,15 +88,21 @@ def get_threads() -> int:
     return int(_load().orc_get_threads())
 
 
+OUTER = {"source": 0, "closed": 1}
+
+
 class Grid:
     """Mesh of nr x nt x np cell-centred unknowns (Sec. 2.2: nonuniform in r
     and theta, periodic in phi).  r faces run from r0 (the photosphere) to r1
-    (the source surface), geometric with cell-width ratio ``ratio`` (1 =
+    (the outer boundary), geometric with cell-width ratio ``ratio`` (1 =
     uniform) unless ``r_faces`` is given; theta faces are uniform unless
-    ``t_faces`` is given."""
+    ``t_faces`` is given.  ``outer``: "source" (source surface, Phi = 0 at r1)
+    or "closed" (closed wall, Br = 0 at r1), Sec. 2.1."""
 
-    def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None):
+    def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
+                 outer="source"):
         self.nr, self.nt, self.np = int(nr), int(nt), int(np_)
+        self.outer = outer
         lib = _load()
         if r_faces is None:
             rf = np.empty(self.nr + 1)
@@ -129,6 +140,7 @@ class Grid:
         return (np.arange(self.np) + 0.5) * (2 * np.pi / self.np)
 
     def _dims(self):
+        _load().orc_set_outer(OUTER[self.outer])
         return self.nr, self.nt, self.np, _p(self.rf), _p(self.tf)
 
     # -- operator (Sec. 2.2, Eq. 4) --------------------------------------
@@ -194,8 +206,26 @@ class Grid:
             return x, it.value, st, hist[: it.value + 1].copy()
         return x, it.value, st
 
+    def balanced_br(self, br: np.ndarray) -> np.ndarray:
+        """The Br the right-hand side uses: for the closed wall, without its
+        area-weighted mean (zero net flux); else unchanged."""
+        br = np.ascontiguousarray(br, dtype=np.float64).reshape(self.nt, self.np)
+        out = np.empty_like(br)
+        _load().orc_balance_br(*self._dims(), _p(br), _p(out))
+        return out
+
+    def remove_mean(self, x: np.ndarray) -> np.ndarray:
+        """x minus its mean over the cells (the closed-wall gauge)."""
+        y = np.array(x, dtype=np.float64, order="C", copy=True)
+        _load().orc_remove_mean(y.size, _p(y))
+        return y
+
     def solve(self, br: np.ndarray, tol: float, maxit: int = 1_000_000):
+        """PCG on b(Br); for the closed wall the result is gauged to zero
+        mean over the cells."""
         x, it, st = self.pcg(self.rhs(br), tol, maxit)
+        if self.outer == "closed":
+            x = self.remove_mean(x)
         return x, it, st
 
     # -- field (Sec. 2.1: B = grad Phi; Eq. 3 at the poles) ----------------

@@ -31,6 +31,13 @@
  *   - Outer boundary r=R_1, source surface Phi=0 (Sec. 2.1): mirror ghost
  *     Phi_ghost = -Phi_c at spacing 2 (R_1 - r_last), i.e. a coupling
  *     2 c^r_outer x_c on the last radial layer.
+ *   - Outer boundary alternative, closed wall Br = dPhi/dr = 0 at R_1
+ *     (Sec. 2.1, orc_set_outer(1)): the outer face carries no flux, like the
+ *     inner face without its Br.  L is then singular (constants are its null
+ *     space); the right-hand side must have zero net flux, so the inner Br
+ *     loses its area-weighted mean (the discrete monopole) before b is
+ *     formed, and a solution is defined up to a constant: orc_remove_mean
+ *     gives the representative with zero mean over the cells.
  *   - Poles (Eq. 3): the pole faces have sin(0) = sin(pi) = 0 area, so they
  *     carry no coupling in L; Eq. 3 enters through the field evaluation,
  *     where the ghost cell across the pole is set so that the face value is
@@ -64,6 +71,15 @@ typedef struct {
 } orc_op;
 
 static int g_threads = 0;
+static int g_outer_closed = 0; /* 0: source surface Phi = 0; 1: closed wall Br = 0 */
+
+/* Outer boundary condition used by every later call: 0 = source surface,
+ * 1 = closed wall. */
+int orc_set_outer(int kind) {
+  if (kind != 0 && kind != 1) return 3;
+  g_outer_closed = kind;
+  return 0;
+}
 
 void orc_set_threads(int n) {
   g_threads = n;
@@ -158,6 +174,8 @@ static int op_build(orc_op *op, int nr, int nt, int np, const double *rf, const 
       double rface = rf[i + 1];
       double spacing = (i < nr - 1) ? (op->rc[i + 1] - op->rc[i]) : 2.0 * (rf[nr] - op->rc[nr - 1]);
       op->cr[i * nt + j] = rface * rface * sin(op->tc[j]) * op->dt[j] * dphi / spacing;
+      /* closed wall: no flux through the outer face */
+      if (i == nr - 1 && g_outer_closed) op->cr[i * nt + j] = 0.0;
       op->cp[i * nt + j] = op->dr[i] * op->dt[j] / (sin(op->tc[j]) * dphi);
     }
     for (int j = 0; j + 1 < nt; j++) {
@@ -274,6 +292,31 @@ int orc_coeffs(int nr, int nt, int np, const double *rf, const double *tf, doubl
   return ORC_OK;
 }
 
+/* Closed wall: Br minus its area-weighted mean over the inner face (the
+ * discrete monopole), so that the right-hand side has zero net flux.  With
+ * the source surface Br is copied unchanged. */
+int orc_balance_br(int nr, int nt, int np, const double *rf, const double *tf, const double *br,
+                   double *out) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  double mono = 0.0;
+  if (g_outer_closed) {
+    double fl = 0.0, ar = 0.0;
+    for (int j = 0; j < nt; j++) {
+      double area = rf[0] * rf[0] * sin(op.tc[j]) * op.dt[j] * op.dphi;
+      for (int k = 0; k < np; k++) {
+        fl += area * br[(long)j * np + k];
+        ar += area;
+      }
+    }
+    mono = fl / ar;
+  }
+  for (long e = 0; e < (long)nt * np; e++) out[e] = br[e] - mono;
+  op_free(&op);
+  return ORC_OK;
+}
+
 /* Right-hand side from the inner-boundary Br map (Eq. 2). */
 int orc_rhs(int nr, int nt, int np, const double *rf, const double *tf, const double *br,
             double *b) {
@@ -282,9 +325,22 @@ int orc_rhs(int nr, int nt, int np, const double *rf, const double *tf, const do
   if (st) return st;
   long n = (long)nr * nt * np;
   memset(b, 0, sizeof(double) * n);
+  /* closed wall: subtract the area-weighted mean of Br (zero net flux) */
+  double mono = 0.0;
+  if (g_outer_closed) {
+    double fl = 0.0, ar = 0.0;
+    for (int j = 0; j < nt; j++) {
+      double area = rf[0] * rf[0] * sin(op.tc[j]) * op.dt[j] * op.dphi;
+      for (int k = 0; k < np; k++) {
+        fl += area * br[(long)j * np + k];
+        ar += area;
+      }
+    }
+    mono = fl / ar;
+  }
   for (int j = 0; j < nt; j++) {
     double area = rf[0] * rf[0] * sin(op.tc[j]) * op.dt[j] * op.dphi;
-    for (int k = 0; k < np; k++) b[(long)j * np + k] = -area * br[(long)j * np + k];
+    for (int k = 0; k < np; k++) b[(long)j * np + k] = -area * (br[(long)j * np + k] - mono);
   }
   op_free(&op);
   return ORC_OK;
@@ -370,6 +426,15 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
   return status;
 }
 
+/* Subtracts the arithmetic mean over all n cells from x: the gauge of the
+ * closed-wall problem, whose solution is defined up to a constant. */
+void orc_remove_mean(long n, double *x) {
+  double s = 0.0;
+  for (long c = 0; c < n; c++) s += x[c];
+  const double m = s / (double)n;
+  for (long c = 0; c < n; c++) x[c] -= m;
+}
+
 /* Pole averages (Eq. 3): mean over phi of the first ring at each radius.
  * north[i] uses j = 0, south[i] uses j = nt-1. */
 int orc_pole_avg(int nr, int nt, int np, const double *phi, double *north, double *south) {
@@ -390,8 +455,10 @@ int orc_pole_avg(int nr, int nt, int np, const double *phi, double *north, doubl
  *   Br  [(nr+1) * nt * np]  on r faces  r_{i+1/2}, i = -1..nr-1 (face index 0..nr)
  *   Bth [nr * (nt+1) * np]  on th faces th_{j+1/2}, j = -1..nt-1 (face index 0..nt)
  *   Bph [nr * nt * np]      on phi faces between k and k+1 (wrapping)
- * Ghosts: inner Phi_g = Phi_0 - Br dr1 (so the inner face gets Br exactly);
- * outer Phi_g = -Phi_last (Phi = 0 on the source surface); across a pole
+ * Ghosts: inner Phi_g = Phi_0 - Br dr1 (so the inner face gets Br exactly;
+ * for the closed wall pass the balanced Br of orc_balance_br, the one the
+ * solve used); outer Phi_g = -Phi_last (Phi = 0 on the source surface) or
+ * Phi_last (closed wall, Br = 0); across a pole
  * Phi_g = 2 avg - Phi_ring, so the pole face value is the ring's phi-average
  * (Eq. 3 with epsilon = half the first cell). */
 int orc_field(int nr, int nt, int np, const double *rf, const double *tf, const double *phi,
@@ -414,7 +481,8 @@ int orc_field(int nr, int nt, int np, const double *rf, const double *tf, const 
           Br[o] = br[(long)j * np + k];
         } else if (f == nr) {
           double pl = phi[((long)(nr - 1) * nt + j) * np + k];
-          double ghost = -pl;
+          /* source surface: ghost -Phi; closed wall: ghost Phi (Br = 0) */
+          double ghost = g_outer_closed ? pl : -pl;
           double spacing = 2.0 * (rf[nr] - op.rc[nr - 1]);
           Br[o] = (ghost - pl) / spacing;
         } else {
