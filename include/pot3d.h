@@ -65,7 +65,12 @@ extern "C" {
 
 /* ---- boundary conditions (Sec. 2.1) ---------------------------------- */
 #define POT3D_OUTER_SOURCE_SURFACE 0 /* Phi = 0 at r = r1                              */
-#define POT3D_OUTER_CLOSED_WALL 1    /* Br = 0 at r = r1: POT3D_ERR_UNSUPPORTED for now */
+#define POT3D_OUTER_CLOSED_WALL 1    /* Br = dPhi/dr = 0 at r = r1.  The operator is then
+                                        singular (constants are its null space): every
+                                        call that forms the right-hand side first removes
+                                        Br's area-weighted mean over the inner face (zero
+                                        net flux), and every returned Phi has zero mean
+                                        over the cells                                  */
 #define POT3D_POLE_AVERAGE 0         /* Eq. 3                                          */
 
 typedef struct pot3d_plan pot3d_plan_t;
@@ -115,6 +120,10 @@ typedef struct {
                          most 10 restarts, within max_iters in total).  stats
                          report the FP64 residual and the restarts (outer_iters).
                          MIXED always stops on the FP64 residual.                */
+  int history;        /* FP64 and FP64_DF: 1 = record the recurrence residual
+                         ||r_k|| / ||b|| of every iteration k = 0 .. iters of the
+                         next solves (with verify: of the last restart), read back
+                         with pot3d_get_history; 0 = off                          */
 } pot3d_opts_t;
 
 /* pot3d_stats_t.flags bits */
@@ -122,6 +131,12 @@ typedef struct {
                                   is above tol although the PCG recurrence
                                   residual met it (the solve still returns
                                   POT3D_OK: the paper's stopping rule)          */
+
+/* Residual history of the last FP64 / FP64_DF solve run with opts.history:
+ * copies min(cap, iters + 1) values ||r_k|| / ||b||, k = 0, 1, ..., into
+ * relres (host) and their count into *n.  POT3D_ERR_INVALID_ARG when no
+ * history was recorded. */
+int pot3d_get_history(const pot3d_plan_t *plan, double *relres, int cap, int *n);
 
 /* Statistics of the last solve on a plan. */
 typedef struct {
@@ -245,9 +260,10 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
  *   br [nt*np], phi [nr*nt*np]   device pointers only (host arrays would need
  *                                a staging copy: POT3D_ERR_INVALID_ARG)
  *   relres                       host, written
- * Allocates nothing: the plan (created beforehand) supplies its tables, and
- * the per-block partial sums go to a 32 KiB scratch array compiled into the
- * library (4096 doubles, room for 2047 blocks; the call launches at most
+ * Allocates nothing: the plan (created beforehand) supplies its tables (and,
+ * with the closed wall, its own buffer for the balanced Br), and the
+ * per-block partial sums go to a 32 KiB scratch array compiled into the
+ * library (4096 doubles, room for 2046 blocks; the call launches at most
  * 4 x SMs blocks and returns POT3D_ERR_TOO_LARGE if that exceeds the room).
  * Every GPU that loads the library holds the array until the process exits.
  * The first call on each device (each device context) looks up the array's

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(NT) k_sum_pairs(const double *part, int n, dou
 // With x0, sums[2], sums[3] hold ||r0||^2 and sum Dinv r0^2 of the unscaled
 // initial residual.
 static __global__ void k_start(SolveState *st, const double *sums, double n0, double tol, int maxit,
-                        int use_x0, double forced_scale) {
+                               int use_x0, double forced_scale, double *hist) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double bb = sums[0];
   double scale = 1.0;
@@ -85,11 +85,13 @@ static __global__ void k_start(SolveState *st, const double *sums, double n0, do
   if (bb == 0.0) {
     st->relres = 0.0;
     st->status = ST_CONVERGED;
+    if (hist) hist[0] = 0.0;
     return;
   }
   const double relres = sqrt(rr * scale * scale) / sqrt(st->bb);
   st->relres = relres;
   st->status = (relres <= tol) ? ST_CONVERGED : ST_RUNNING;
+  if (hist) hist[0] = relres;
 }
 
 // Residual replacement of the refinement loop (reliable update): the inner
@@ -284,6 +286,64 @@ static __global__ void k_unpad(const double *__restrict__ src, int spitch, doubl
   }
 }
 
+// ------------------------------------------------- closed-wall boundary
+// With the closed wall (Br = 0 at the outer face, Sec. 2.1) the operator's
+// null space is the constants: the right-hand side must carry zero net flux
+// and the solution is fixed up to a constant.
+
+// Block partials of the inner-face flux sum_jk S_j Br_jk, as pairs (flux, 0)
+// for k_sum_pairs.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    k_flux(const double *__restrict__ br, const double *__restrict__ S, int nt, int np,
+           double *part) {
+  __shared__ double red[NT / 32];
+  const size_t n0 = (size_t)nt * np;
+  double f = 0.0;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n0; e += (size_t)gridDim.x * NT) {
+    const int j = (int)(e / np);
+    f = fma(S[j], br[e], f);
+  }
+  const double t = block_sum<NT>(f, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// out = br - sum[0] * inv_area: Br without its area-weighted mean (the
+// discrete monopole), so that b has zero net flux.
+static __global__ void k_shift(const double *__restrict__ br, double *__restrict__ out, size_t n0,
+                               const double *sum, double inv_area) {
+  const double m = __ldcg(sum) * inv_area;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n0;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[e] = br[e] - m;
+}
+
+// Block partials of sum x (dense, n values), as pairs (sum, 0).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sum_partials(const double *__restrict__ x, size_t n,
+                                                     double *part) {
+  __shared__ double red[NT / 32];
+  double s = 0.0;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT)
+    s += x[e];
+  const double t = block_sum<NT>(s, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// The closed-wall gauge: x -= sum[0] / n (zero mean over the cells).
+static __global__ void k_sub_mean(double *__restrict__ x, size_t n, const double *sum, double inv_n) {
+  const double m = __ldcg(sum) * inv_n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    x[e] -= m;
+}
+
 // ------------------------------------------------------------------ field
 // Pole averages (Eq. 3): poles[2 i] = mean_k Phi[i][0][k] (north),
 // poles[2 i + 1] = mean_k Phi[i][nt-1][k] (south).  One block per (i, pole).
@@ -308,57 +368,47 @@ __global__ void __launch_bounds__(NT)
 //   irc [nr]  : 1 / r_i          isd [nt]: 1 / (sin th_j dphi)
 struct FieldTabs {
   const double *irs, *its, *irc, *isd;
+  int closed; // closed wall: Br = 0 on the outer face
 };
 
 // B = grad Phi on the staggered faces; see the header for the layout.
-static __global__ void k_field(const double *__restrict__ phi, const double *__restrict__ br,
-                        const double *__restrict__ poles, FieldTabs T, int nr, int nt, int np,
-                        double *__restrict__ B) {
-  const size_t nrf = (size_t)(nr + 1) * nt * np;
-  const size_t ntf = (size_t)nr * (nt + 1) * np;
-  const size_t npf = (size_t)nr * nt * np;
-  const size_t tot = nrf + ntf + npf;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
-       e += (size_t)gridDim.x * blockDim.x) {
-    double v;
-    if (e < nrf) {
-      const size_t rowf = e / np;
-      const int k = (int)(e - rowf * np);
-      const int f = (int)(rowf / nt), j = (int)(rowf - (size_t)f * nt);
-      if (f == 0) {
-        v = br[(size_t)j * np + k]; // ghost chosen so that dPhi/dr = Br (Eq. 2)
-      } else if (f == nr) {
-        const double pl = phi[((size_t)(nr - 1) * nt + j) * np + k];
-        v = (-2.0 * pl) * T.irs[nr]; // ghost -Phi: Phi = 0 on the source surface
-      } else {
-        const double lo = phi[((size_t)(f - 1) * nt + j) * np + k];
-        const double hi = phi[((size_t)f * nt + j) * np + k];
-        v = (hi - lo) * T.irs[f];
-      }
-    } else if (e < nrf + ntf) {
-      const size_t e2 = e - nrf;
-      const size_t rowf = e2 / np;
-      const int k = (int)(e2 - rowf * np);
-      const int i = (int)(rowf / (nt + 1)), f = (int)(rowf - (size_t)i * (nt + 1));
-      const double *ph = phi + (size_t)i * nt * np;
-      if (f == 0) {
-        // ghost 2 avg - Phi: the pole-face value is the ring's phi-average (Eq. 3)
-        v = 2.0 * (ph[k] - poles[2 * i]) * T.its[0] * T.irc[i];
-      } else if (f == nt) {
-        v = 2.0 * (poles[2 * i + 1] - ph[(size_t)(nt - 1) * np + k]) * T.its[nt] * T.irc[i];
-      } else {
-        v = (ph[(size_t)f * np + k] - ph[(size_t)(f - 1) * np + k]) * T.its[f] * T.irc[i];
-      }
-    } else {
-      const size_t e3 = e - nrf - ntf;
-      const size_t row = e3 / np;
-      const int k = (int)(e3 - row * np);
-      const int i = (int)(row / nt), j = (int)(row - (size_t)i * nt);
-      const double *ph = phi + row * np;
+// A block takes one (i, j) row of cells at a time (grid-stride over the
+// rows), its threads the phi index k, and writes every face the row owns:
+// the radial face below it (i), the colatitude face north of it (j) and the
+// phi face after each cell; the last radial layer also writes the outer
+// face and the last colatitude row the south pole face.  Phi is read once
+// from HBM (the neighbouring rows come from L2) and every write is
+// coalesced; no 64-bit division in the index arithmetic.
+constexpr int kFieldThreads = 128;
+static __global__ void __launch_bounds__(kFieldThreads)
+    k_field(const double *__restrict__ phi, const double *__restrict__ br,
+            const double *__restrict__ poles, FieldTabs T, int nr, int nt, int np,
+            double *__restrict__ B) {
+  const size_t rplane = (size_t)nt * np;          // one radial layer of Phi / Br faces
+  double *const Bt = B + (size_t)(nr + 1) * rplane; // colatitude faces [nr][nt+1][np]
+  double *const Bp = Bt + (size_t)nr * (nt + 1) * np;
+  for (int q = blockIdx.x; q < nr * nt; q += gridDim.x) {
+    const int i = q / nt, j = q - i * nt;
+    const double *ph = phi + (size_t)q * np;
+    double *br_o = B + (size_t)q * np;                            // radial face i
+    double *bt_o = Bt + ((size_t)i * (nt + 1) + j) * np;          // colatitude face j
+    double *bp_o = Bp + (size_t)q * np;
+    const double ir = T.irc[i], irs = T.irs[i], itj = T.its[j], isd = T.isd[j];
+    for (int k = threadIdx.x; k < np; k += kFieldThreads) {
+      const double v = ph[k];
+      // ghost chosen so that dPhi/dr = Br on the inner face (Eq. 2)
+      br_o[k] = (i == 0) ? br[(size_t)j * np + k] : (v - ph[(ptrdiff_t)k - (ptrdiff_t)rplane]) * irs;
+      // ghost 2 avg - Phi across the north pole: the face value is the
+      // ring's phi-average (Eq. 3)
+      bt_o[k] = (j == 0) ? 2.0 * (v - poles[2 * i]) * T.its[0] * ir : (v - ph[k - np]) * itj * ir;
       const int kp = (k + 1 == np) ? 0 : k + 1;
-      v = (ph[kp] - ph[k]) * T.irc[i] * T.isd[j];
+      bp_o[k] = (ph[kp] - v) * ir * isd;
+      if (i == nr - 1) {
+        // source surface: ghost -Phi (Phi = 0 there); closed wall: ghost Phi
+        br_o[(size_t)rplane + k] = T.closed ? 0.0 : (-2.0 * v) * T.irs[nr];
+      }
+      if (j == nt - 1) bt_o[np + k] = 2.0 * (poles[2 * i + 1] - v) * T.its[nt] * ir;
     }
-    B[e] = v;
   }
 }
 

@@ -141,8 +141,10 @@ int grid_for(const Batch *B, size_t n) {
 size_t slot_bytes(const Plan *P, int nsm) {
   const ArithData &D = P->ar[AR_F32];
   const size_t v4 = al(P->npad * 4), v8 = al(P->npad * 8);
+  // closed wall: a balanced copy of Br
+  const size_t brb = P->closed ? al(sizeof(double) * P->nt * P->np) : 0;
   return 5 * v4 + 2 * v8 + al(sizeof(double) * D.tiles_a) + al(sizeof(double) * 2 * D.tiles_b) +
-         al(sizeof(double) * 2 * 4 * nsm);
+         al(sizeof(double) * 2 * 4 * nsm) + brb;
 }
 
 // Rebuild and upload the concatenated work lists of the occupied slots:
@@ -256,7 +258,7 @@ void launch_inner_start(Batch *B, int s, double new_scale) {
     cudaMemsetAsync(S.v32[4], 0, v4, B->stream);
     const int maxit = B->opts.max_iters > 0 ? B->opts.max_iters : default_maxit(P);
     k_start<<<1, 1, 0, B->stream>>>(B->d_states + s, B->d_isums + 2 * s, (double)P->n, inner_tol,
-                                    maxit, 0, 1.0);
+                                    maxit, 0, 1.0, nullptr);
   }
   S.scale = new_scale;
 }
@@ -320,6 +322,7 @@ int advance_outer(Batch *B, bool starting_only) {
       Plan *P = S.plan;
       k_unpad<<<grid_for(B, P->n), kBThreads, 0, B->stream>>>(S.x64, P->pitch, S.phi, P->np, P->R,
                                                               P->np);
+      gauge_phi(P, S.phi, S.part_aux, B->d_isums + 2 * s, B->stream);
       S.phase = PH_DONE;
       B->dirty = true;
       B->finished.push_back(s);
@@ -468,6 +471,13 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   S.part_b = reinterpret_cast<double *>(p);
   p += al(sizeof(double) * 2 * D.tiles_b);
   S.part_aux = reinterpret_cast<double *>(p);
+  p += al(sizeof(double) * 2 * 4 * B->nsm);
+  if (P->closed) {
+    // the balanced Br this solve uses (zero net flux)
+    double *brb = reinterpret_cast<double *>(p);
+    prepare_br(P, br, brb, S.part_aux, B->d_isums + 2 * s, B->stream);
+    S.br = brb;
+  }
   // descriptor and TMA maps of the slot
   ProbDev &h = B->h_probs[s];
   h = ProbDev{};
@@ -512,7 +522,7 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   cudaMemsetAsync(B->arena_base + off, 0, 5 * v4 + 2 * v8, st);
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = grid_for(B, n0);
-  k_bstats<kBThreads><<<gb, kBThreads, 0, st>>>(br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+  k_bstats<kBThreads><<<gb, kBThreads, 0, st>>>(S.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
                                                 S.part_aux);
   k_sum_pairs<kBThreads><<<1, kBThreads, 0, st>>>(S.part_aux, gb, B->d_sums + 4 * s);
   SolveState idle{};

@@ -10,7 +10,7 @@ const MvVariant *mv_variants_df(int *count) {
   return v;
 }
 
-KLaunch update_launcher_df() { return &up_launch<PDF>; }
-int update_occupancy_df() { return up_occupancy<PDF>(); }
+KLaunch update_launcher_df() { return &up_launch<PDF, kUpdThreadsDF, kUpdSegBytes, kUpdStagesDF>; }
+int update_occupancy_df() { return up_occupancy<PDF, kUpdThreadsDF, kUpdSegBytes, kUpdStagesDF>(); }
 
 } // namespace pot3d

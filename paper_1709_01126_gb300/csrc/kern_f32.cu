@@ -11,8 +11,8 @@ const MvVariant *mv_variants_f32(int *count) {
   return v;
 }
 
-KLaunch update_launcher_f32() { return &up_launch<PF32>; }
-int update_occupancy_f32() { return up_occupancy<PF32>(); }
+KLaunch update_launcher_f32() { return &up_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>; }
+int update_occupancy_f32() { return up_occupancy<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>(); }
 
 // Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
 const MvVariant *mv_variants_f64(int *count);

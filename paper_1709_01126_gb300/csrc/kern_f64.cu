@@ -10,7 +10,7 @@ const MvVariant *mv_variants_f64(int *count) {
   return v;
 }
 
-KLaunch update_launcher_f64() { return &up_launch<PF64>; }
-int update_occupancy_f64() { return up_occupancy<PF64>(); }
+KLaunch update_launcher_f64() { return &up_launch<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>; }
+int update_occupancy_f64() { return up_occupancy<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>(); }
 
 } // namespace pot3d

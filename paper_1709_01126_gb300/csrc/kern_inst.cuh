@@ -46,33 +46,35 @@ MvVariant make_variant() {
   return v;
 }
 
-template <class A>
+// Update kernel configurations: NT threads, SEGB-byte segments, STG stages
+// per warp (stages - 1 segments of r and q in flight per warp).
+template <class A, int NT, int SEGB, int STG>
 void up_setup() {
-  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
+  using LY = UpLayout<NT, SEGB, STG>;
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_update<A, kUpdThreads, kUpdSegBytes>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, LY::BYTES);
+    cudaFuncSetAttribute(k_update<A, NT, SEGB, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         LY::BYTES);
     done = true;
   }
 }
 
-template <class A>
+template <class A, int NT, int SEGB, int STG>
 void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
                cudaStream_t s) {
-  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
-  up_setup<A>();
-  k_update<A, kUpdThreads, kUpdSegBytes><<<grid, kUpdThreads, LY::BYTES, s>>>(probs, work, nwork);
+  using LY = UpLayout<NT, SEGB, STG>;
+  up_setup<A, NT, SEGB, STG>();
+  k_update<A, NT, SEGB, STG><<<grid, NT, LY::BYTES, s>>>(probs, work, nwork);
 }
 
 // resident blocks of the update kernel per SM (0 if the query fails)
-template <class A>
+template <class A, int NT, int SEGB, int STG>
 int up_occupancy() {
-  using LY = UpLayout<kUpdThreads, kUpdSegBytes>;
-  up_setup<A>();
+  using LY = UpLayout<NT, SEGB, STG>;
+  up_setup<A, NT, SEGB, STG>();
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<A, kUpdThreads, kUpdSegBytes>,
-                                                    kUpdThreads, LY::BYTES) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<A, NT, SEGB, STG>, NT,
+                                                    LY::BYTES) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -82,6 +82,9 @@ struct ProbDev {
   double *part_b;    // [2*tiles_b]
   SolveState *st;
   const TmaSet *tma;
+  double *hist;       // residual history [hist_cap] (null: not recorded)
+  int hist_cap;
+  int pad2_;
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -584,41 +587,43 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 
-// Shared memory of k_update: per warp two stages of (r, q) segments of
-// SEGB bytes each, then two mbarriers per warp.
-template <int NT, int SEGB>
+// Shared memory of k_update: per warp STG stages of (r, q) segments of
+// SEGB bytes each, then STG mbarriers per warp.
+template <int NT, int SEGB, int STG>
 struct UpLayout {
   static constexpr int NW = NT / 32;
-  static constexpr int WARP_BYTES = 2 * 2 * SEGB;
-  static constexpr int BYTES = NW * WARP_BYTES + NW * 2 * 8;
+  static constexpr int WARP_BYTES = STG * 2 * SEGB;
+  static constexpr int BYTES = NW * WARP_BYTES + NW * STG * 8;
 };
 
 // Work item = (problem, block of rows_b phi rows).  Each warp walks its rows
-// (row0 + warp, + NW, ...) in segments of at most SEGB bytes: lane 0 issues
-// cp.async.bulk copies of the r and q segments into the warp's next stage
-// while the warp computes the current one (two stages per warp, completion
-// counted by mbarriers, waits bounded by the global timer).  r -= alpha q is
-// written back from registers; per row s = sum r^2, then ||r||^2 += s and
-// rho += D^-1 s.  The last block closes the iteration.
-template <class A, int NT, int SEGB>
+// (row0 + warp, + NW, ...) in segments of at most SEGB bytes: lane 0 keeps
+// STG - 1 segments of r and q in flight ahead of the one the warp computes
+// (cp.async.bulk into the warp's stages, completion counted by one mbarrier
+// per stage, waits bounded by the global timer).  A cursor (row, i, j,
+// segment) advances without divisions; the row's D^-1 weight is fetched
+// before its first segment is awaited.  r -= alpha q is written back from
+// registers; per row s = sum r^2, then ||r||^2 += s and rho += D^-1 s.  The
+// last block closes the iteration.
+template <class A, int NT, int SEGB, int STG>
 __global__ void __launch_bounds__(NT)
     k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
              const int *__restrict__ nwork_p) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
-  using LY = UpLayout<NT, SEGB>;
+  using LY = UpLayout<NT, SEGB, STG>;
   constexpr int V = A::kVec, NW = NT / 32, ES = (int)sizeof(st), SEG = SEGB / ES;
   static_assert(SEG % (32 * V) == 0, "segment must be whole warp-vectors");
+  static_assert(STG >= 2, "at least one segment in flight ahead");
   extern __shared__ __align__(128) unsigned char smu[];
   __shared__ double red[NW];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, tid = threadIdx.x;
   st *wbuf = reinterpret_cast<st *>(smu + wy * LY::WARP_BYTES); // [stage][r|q][SEG]
-  uint64_t *wbar = reinterpret_cast<uint64_t *>(smu + NW * LY::WARP_BYTES) + 2 * wy;
+  uint64_t *wbar = reinterpret_cast<uint64_t *>(smu + NW * LY::WARP_BYTES) + STG * wy;
   if (lane == 0) {
-    mbar_init(&wbar[0], 1);
-    mbar_init(&wbar[1], 1);
+    for (int g = 0; g < STG; g++) mbar_init(&wbar[g], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -643,36 +648,61 @@ __global__ void __launch_bounds__(NT)
     const int nseg = (np + SEG - 1) / SEG;
     const int nrows_w = (row1 - row0 - wy + NW - 1) / NW;
     const int units = nrows_w > 0 ? nrows_w * nseg : 0;
-    auto unit_row = [&](int u) { return row0 + wy + NW * (u / nseg); };
-    auto unit_off = [&](int u) {
-      const int row = unit_row(u), i = row / nt, j = row - i * nt;
-      return (size_t)i * plane + (size_t)j * pitch + (size_t)(u % nseg) * SEG;
+    // a cursor over this warp's units: row (i, j) and segment
+    struct Cur {
+      int i, j, seg;
+      size_t off;
     };
-    auto unit_len = [&](int u) { return min(SEG, np - (u % nseg) * SEG); };
+    auto start = [&](int row) {
+      Cur c;
+      c.i = row / nt;
+      c.j = row - c.i * nt;
+      c.seg = 0;
+      c.off = (size_t)c.i * plane + (size_t)c.j * pitch;
+      return c;
+    };
+    auto advance = [&](Cur &c) {
+      if (++c.seg == nseg) {
+        c.seg = 0;
+        c.j += NW;
+        while (c.j >= nt) {
+          c.j -= nt;
+          c.i++;
+        }
+        c.off = (size_t)c.i * plane + (size_t)c.j * pitch;
+      }
+    };
+    Cur ci = start(row0 + wy); // next unit to issue
+    Cur cc = ci;               // next unit to compute
     auto issue = [&](int u) {
       if (lane == 0) {
-        const uint32_t stg = (useq + u) & 1u;
-        const uint32_t bytes = (uint32_t)((unit_len(u) * ES + 15) & ~15);
-        const size_t off = unit_off(u);
+        const uint32_t stg = (useq + u) % STG;
+        const int len = min(SEG, np - ci.seg * SEG);
+        const uint32_t bytes = (uint32_t)((len * ES + 15) & ~15);
+        const size_t off = ci.off + (size_t)ci.seg * SEG;
         mbar_expect_tx(&wbar[stg], 2 * bytes);
         bulk_load(wbuf + (2 * stg) * SEG, r + off, bytes, &wbar[stg]);
         bulk_load(wbuf + (2 * stg + 1) * SEG, q + off, bytes, &wbar[stg]);
       }
+      advance(ci);
     };
     bool bad = false;
-    if (units > 0) issue(0);
+    int issued = 0;
+    for (; issued < min(units, STG - 1); issued++) issue(issued);
     int u = 0;
+    coef wrow{};
     for (; u < units; u++) {
-      if (u + 1 < units) issue(u + 1);
-      const uint32_t stg = (useq + u) & 1u;
-      if (!mbar_wait(&wbar[stg], ((useq + u) >> 1) & 1u)) {
+      if (issued < units) issue(issued++);
+      if (cc.seg == 0) wrow = cf[(size_t)cc.i * ntp + cc.j]; // ahead of the wait
+      const uint32_t stg = (useq + u) % STG;
+      if (!mbar_wait(&wbar[stg], ((useq + u) / STG) & 1u)) {
         bad = true;
         break;
       }
       const st *rs = wbuf + (2 * stg) * SEG;
       const st *qs = wbuf + (2 * stg + 1) * SEG;
-      const int len = unit_len(u);
-      const size_t off = unit_off(u);
+      const int len = min(SEG, np - cc.seg * SEG);
+      const size_t off = cc.off + (size_t)cc.seg * SEG;
       for (int k = lane * V; k < len; k += 32 * V) {
         val rv[V], qv[V];
 #pragma unroll
@@ -688,18 +718,19 @@ __global__ void __launch_bounds__(NT)
         A::stvv(r + off + k, rv);
       }
       __syncwarp();
-      if (u % nseg == nseg - 1) {
-        const int row = unit_row(u), i = row / nt, j = row - i * nt;
+      if (cc.seg == nseg - 1) {
         A::d_merge(arr, s);
-        A::d_addw(arho, cf[(size_t)i * ntp + j], s);
+        A::d_addw(arho, wrow, s);
         s = A::d_init();
       }
+      advance(cc);
     }
     if (bad) {
-      // drain this warp's copy still in flight (bounded), then report
-      if (u + 1 < units) mbar_wait(&wbar[(useq + u + 1) & 1u], ((useq + u + 1) >> 1) & 1u);
+      // drain this warp's copies still in flight (bounded), then report
+      for (int v = u; v < issued; v++)
+        mbar_wait(&wbar[(useq + v) % STG], ((useq + v) / STG) & 1u);
     }
-    useq += units;
+    useq += issued;
     if (__syncthreads_or(bad)) {
       if (tid == 0) stt->status = ST_TIMEOUT;
       break;
@@ -723,6 +754,7 @@ __global__ void __launch_bounds__(NT)
         stt->relres = relres;
         stt->rr = rr;
         stt->iter = kit;
+        if (P.hist && kit < P.hist_cap) P.hist[kit] = relres;
         if (!isfinite(relres)) {
           stt->status = ST_BREAKDOWN;
         } else if (relres <= stt->tol) {

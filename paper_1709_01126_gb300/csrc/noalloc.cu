@@ -31,7 +31,7 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 namespace {
 
 constexpr int kNoAllocThreads = 256;
-constexpr int kNoAllocMaxBlocks = (kNoAllocScratchDoubles - 2) / 2;
+constexpr int kNoAllocMaxBlocks = (kNoAllocScratchDoubles - 4) / 2;
 constexpr int kMaxDevices = 64;
 
 // Device addresses of the array, one per device, looked up with
@@ -164,7 +164,14 @@ extern "C" int pot3d_residual_noalloc(pot3d_plan_t *plan, const double *br, cons
   if (rc) return rc;
   cudaStream_t s = P->stream;
   // every slot read below is written first by this call: nothing to clear
-  k_noalloc_partials<<<nblk, kNoAllocThreads, 0, s>>>(br, phi, P->d_S, P->d_c64, P->nr, P->nt,
+  const double *brs = br;
+  if (P->closed) {
+    // closed wall: the balanced Br (zero net flux), in the plan's own
+    // buffer; the flux partials and their sum use the scratch
+    prepare_br(P, br, P->d_br_tmp, scratch, scratch + kNoAllocScratchDoubles - 4, s);
+    brs = P->d_br_tmp;
+  }
+  k_noalloc_partials<<<nblk, kNoAllocThreads, 0, s>>>(brs, phi, P->d_S, P->d_c64, P->nr, P->nt,
                                                       P->np, scratch);
   k_noalloc_final<<<1, kNoAllocThreads, 0, s>>>(scratch, nblk);
   cudaError_t e = cudaGetLastError();

@@ -60,8 +60,13 @@ struct Plan {
   double *h_sums = nullptr;    // pinned [8]
   SolveState *h_state = nullptr; // pinned, two snapshots: [0] is the final state of a solve
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
-  double *d_br_last = nullptr;
+  double *d_br_last = nullptr; // Br of the last solve (closed wall: balanced)
   bool have_br = false;
+  // closed wall (Br = 0 at r1): the operator is singular; Br is balanced to
+  // zero net flux and Phi gauged to zero mean
+  bool closed = false;
+  double inv_area = 0.0;        // 1 / (np sum_j S_j): inner-face area
+  double *d_br_tmp = nullptr;   // balanced copy of a Br given to field / residual
   double *d_stage = nullptr;
   size_t stage_bytes = 0;
   cudaStream_t stream = nullptr, own_stream = nullptr, user_stream = nullptr;
@@ -70,6 +75,8 @@ struct Plan {
   int nsm = 0;
   std::vector<cudaEvent_t> ev;
   bool freeze_poll = false; // testing hook: the host re-reads a stale state snapshot
+  double *d_hist = nullptr;  // residual history of the last PCG run (opts.history)
+  int hist_alloc = 0, hist_n = 0;
 };
 
 int fail(int code);
@@ -95,5 +102,12 @@ int default_maxit(const Plan *P);
 // Inner tolerance of mixed refinement when the options give none.
 double default_inner_tol(const Plan *P, bool restart);
 int segment_cap(const Plan *P);
+// Br prepared for the right-hand side on stream s: a copy (source surface)
+// or Br without its area-weighted mean (closed wall), written to out;
+// part holds at least 2 * 4 * nsm doubles of block partials, sum one double pair.
+void prepare_br(const Plan *P, const double *br, double *out, double *part, double *sum,
+                cudaStream_t s);
+// The closed-wall gauge of a dense Phi on stream s (no-op for the source surface).
+void gauge_phi(const Plan *P, double *phi, double *part, double *sum, cudaStream_t s);
 
 } // namespace pot3d

@@ -100,8 +100,9 @@ static int build_mesh(Plan *P, const pot3d_grid_t *g) {
 //   c^th on face th_{j+1/2} = dr_i sin th_{j+1/2} dphi / (th_{j+1} - th_j)
 //   c^ph                    = dr_i dth_j / (sin th_j dphi)
 // Boundary faces: the inner face carries the Br flux (right-hand side), the
-// source surface couples to the ghost -Phi (adds 2 c^r to D), the pole
-// faces have zero area (sin 0 = sin pi = 0).
+// source surface couples to the ghost -Phi (adds 2 c^r to D; the closed wall
+// carries no flux and adds nothing), the pole faces have zero area
+// (sin 0 = sin pi = 0).
 static void build_tables(Plan *P) {
   const int nr = P->nr, nt = P->nt;
   const size_t R = P->R;
@@ -120,7 +121,7 @@ static void build_tables(Plan *P) {
       const double rp = P->rf[i + 1], rm = P->rf[i];
       double out = 0.0;
       if (i + 1 < nr) cRp[row] = rp * rp * ang / (P->rc[i + 1] - P->rc[i]);
-      else out = 2.0 * (rp * rp * ang / (2.0 * (P->rf[nr] - P->rc[nr - 1])));
+      else if (!P->closed) out = 2.0 * (rp * rp * ang / (2.0 * (P->rf[nr] - P->rc[nr - 1])));
       if (i > 0) cRm[row] = rm * rm * ang / (P->rc[i] - P->rc[i - 1]);
       if (j + 1 < nt) cTp[row] = P->drc[i] * sf[j + 1] * dphi / (P->tc[j + 1] - P->tc[j]);
       if (j > 0) cTm[row] = P->drc[i] * sf[j] * dphi / (P->tc[j] - P->tc[j - 1]);
@@ -131,7 +132,12 @@ static void build_tables(Plan *P) {
   }
   P->S.resize(nt);
   const double r0 = P->rf[0];
-  for (int j = 0; j < nt; j++) P->S[j] = r0 * r0 * sc[j] * P->dtc[j] * dphi;
+  double area = 0.0;
+  for (int j = 0; j < nt; j++) {
+    P->S[j] = r0 * r0 * sc[j] * P->dtc[j] * dphi;
+    area += P->S[j];
+  }
+  P->inv_area = 1.0 / (area * P->np);
   // field tables
   P->irs.assign(nr + 1, 0.0);
   for (int f = 1; f < nr; f++) P->irs[f] = 1.0 / (P->rc[f] - P->rc[f - 1]);
@@ -294,12 +300,12 @@ pot3d_plan_t *pot3d_plan(const pot3d_grid_t *g, const pot3d_bc_t *bc) {
     return nullptr;
   }
   if (bc) {
-    if (bc->outer == POT3D_OUTER_CLOSED_WALL || bc->pole != POT3D_POLE_AVERAGE) {
-      fail(POT3D_ERR_UNSUPPORTED);
+    if (bc->outer != POT3D_OUTER_SOURCE_SURFACE && bc->outer != POT3D_OUTER_CLOSED_WALL) {
+      fail(POT3D_ERR_INVALID_ARG);
       return nullptr;
     }
-    if (bc->outer != POT3D_OUTER_SOURCE_SURFACE) {
-      fail(POT3D_ERR_INVALID_ARG);
+    if (bc->pole != POT3D_POLE_AVERAGE) {
+      fail(POT3D_ERR_UNSUPPORTED);
       return nullptr;
     }
   }
@@ -318,6 +324,7 @@ pot3d_plan_t *pot3d_plan(const pot3d_grid_t *g, const pot3d_bc_t *bc) {
   P->pitch = (g->np + 31) / 32 * 32;
   P->ntp = (g->nt + 3) / 4 * 4;
   P->npad = P->R * P->pitch;
+  P->closed = bc && bc->outer == POT3D_OUTER_CLOSED_WALL;
   int rc = build_mesh(P, g);
   if (rc) {
     delete P;

@@ -51,6 +51,7 @@ int plan_device_init(Plan *P) {
   CTRY(up(&P->d_isd, P->isd));
   CTRY(cudaMalloc(&P->d_poles, sizeof(double) * 2 * P->nr));
   CTRY(cudaMalloc(&P->d_br_last, sizeof(double) * P->nt * P->np));
+  if (P->closed) CTRY(cudaMalloc(&P->d_br_tmp, sizeof(double) * P->nt * P->np));
   P->aux_blocks = 4 * P->nsm;
   CTRY(cudaMalloc(&P->d_part, sizeof(double) * 2 * P->aux_blocks));
   CTRY(cudaMalloc(&P->d_sums, sizeof(double) * 8));
@@ -86,6 +87,8 @@ void plan_free(Plan *P) {
   cudaFree(P->d_isd);
   cudaFree(P->d_poles);
   cudaFree(P->d_br_last);
+  cudaFree(P->d_br_tmp);
+  cudaFree(P->d_hist);
   cudaFree(P->d_part);
   cudaFree(P->d_sums);
   cudaFree(P->d_stage);
@@ -436,6 +439,27 @@ static int status_code(int st) {
 
 int default_maxit(const Plan *P) { return 100 * (P->nr + P->nt + P->np); }
 
+void prepare_br(const Plan *P, const double *br, double *out, double *part, double *sum,
+                cudaStream_t s) {
+  const size_t n0 = (size_t)P->nt * P->np;
+  if (!P->closed) {
+    if (out != br) cudaMemcpyAsync(out, br, n0 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return;
+  }
+  const int g = aux_grid(P, n0);
+  k_flux<kAuxThreads><<<g, kAuxThreads, 0, s>>>(br, P->d_S, P->nt, P->np, part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(part, g, sum);
+  k_shift<<<g, kAuxThreads, 0, s>>>(br, out, n0, sum, P->inv_area);
+}
+
+void gauge_phi(const Plan *P, double *phi, double *part, double *sum, cudaStream_t s) {
+  if (!P->closed) return;
+  const int g = aux_grid(P, P->n);
+  k_sum_partials<kAuxThreads><<<g, kAuxThreads, 0, s>>>(phi, P->n, part);
+  k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(part, g, sum);
+  k_sub_mean<<<g, kAuxThreads, 0, s>>>(phi, P->n, sum, 1.0 / (double)P->n);
+}
+
 // Iterations one continued inner segment may take before it is ended and
 // the next refinement step restarts the inner PCG from zero.
 int segment_cap(const Plan *P) { return 20 * (P->nr + P->nt + P->np); }
@@ -493,32 +517,52 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   fill_prob<A>(P, ai, x, r, p0, p1, q);
   TRY(build_tma(P, ai));
   cudaStream_t s = P->stream;
-  CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
-  CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
-                       cudaMemcpyDeviceToDevice, s));
+  // the Br of the right-hand side (closed wall: balanced), kept for the field
+  prepare_br(P, io.br, P->d_br_last, P->d_part, P->d_sums + 6, s);
+  const double *brs = P->d_br_last;
   P->have_br = true;
   CTRY(cudaMemsetAsync(P->ws, 0, 5 * ((P->npad * es + 255) & ~(size_t)255), s));
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = aux_grid(P, n0);
-  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(brs, P->d_S, P->d_c64, P->nr, P->nt, P->np,
                                                    P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
   if (x0) {
     const int g = aux_grid(P, P->n);
-    k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+    k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, brs, P->d_S, P->d_c64, P->nr,
                                                   P->nt, P->np, 0, (double *)q, P->pitch,
                                                   P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
   }
   const int maxit = P->opts.max_iters > 0 ? P->opts.max_iters : default_maxit(P);
-  k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums, (double)n0, tol, maxit, x0 ? 1 : 0, 0.0);
+  P->hist_n = 0;
+  if (P->opts.history) {
+    if (P->hist_alloc < maxit + 1) {
+      cudaFree(P->d_hist);
+      P->d_hist = nullptr;
+      P->hist_alloc = 0;
+      if (cudaMalloc(&P->d_hist, sizeof(double) * (maxit + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(POT3D_ERR_OOM);
+      }
+      P->hist_alloc = maxit + 1;
+    }
+    D.h_prob.hist = P->d_hist;
+    D.h_prob.hist_cap = maxit + 1;
+  } else {
+    D.h_prob.hist = nullptr;
+    D.h_prob.hist_cap = 0;
+  }
+  CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+  k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums, (double)n0, tol, maxit, x0 ? 1 : 0, 0.0,
+                          P->opts.history ? P->d_hist : nullptr);
   if (x0) {
     k_x0_setup<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(
         (const double *)q, io.phi, P->d_c64, P->nr, P->nt, P->np, P->pitch, D.d_state,
         (typename A::st *)r, (typename A::st *)x);
     CTRY(cudaMemsetAsync(q, 0, P->npad * es, s));
   } else {
-    k_write_rhs<A><<<aux_grid(P, n0), kAuxThreads, 0, s>>>(io.br, P->d_S, P->nt, P->np, P->pitch,
+    k_write_rhs<A><<<aux_grid(P, n0), kAuxThreads, 0, s>>>(brs, P->d_S, P->nt, P->np, P->pitch,
                                                            D.d_state, (typename A::st *)r);
   }
   CTRY(cudaGetLastError());
@@ -527,9 +571,10 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   TRY(iterate<A>(P, ai));
   P->stats.launches += 1;
   k_finish<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, io.phi, 1);
+  gauge_phi(P, io.phi, P->d_part, P->d_sums + 6, s);
   // the FP64 residual of the returned Phi (||b||^2 is in d_sums[0])
   const int g = aux_grid(P, P->n);
-  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, brs, P->d_S, P->d_c64, P->nr,
                                                 P->nt, P->np, 0, nullptr, P->np, P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
   P->stats.launches += 2;
@@ -548,6 +593,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   const double bb = P->h_sums[0];
   P->stats.relres_fp64 = bb > 0 ? std::sqrt(P->h_sums[2]) / std::sqrt(bb) : 0.0;
   P->stats.flags = (P->stats.status == POT3D_OK && P->stats.relres_fp64 > tol) ? POT3D_FLAG_ABOVE_TOL : 0;
+  if (P->opts.history) P->hist_n = std::min(hs.iter + 1, P->hist_alloc);
   if (iters) *iters = hs.iter;
   return P->stats.status ? fail(P->stats.status) : POT3D_OK;
 }
@@ -568,8 +614,9 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q);
   TRY(build_tma(P, AR_F32));
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
-  CTRY(cudaMemcpyAsync(P->d_br_last, io.br, sizeof(double) * P->nt * P->np,
-                       cudaMemcpyDeviceToDevice, s));
+  // the Br of the right-hand side (closed wall: balanced), kept for the field
+  prepare_br(P, io.br, P->d_br_last, P->d_part, P->d_sums + 6, s);
+  const double *brs = P->d_br_last;
   P->have_br = true;
   const size_t v4 = (P->npad * 4 + 255) & ~(size_t)255;
   CTRY(cudaMemsetAsync(P->ws, 0, 5 * v4, s));
@@ -579,7 +626,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     k_unpad<<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(io.phi, P->np, x64, P->pitch, P->R, P->np);
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = aux_grid(P, n0);
-  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(brs, P->d_S, P->d_c64, P->nr, P->nt, P->np,
                                                    P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
   const int gn = aux_grid(P, P->n);
@@ -594,7 +641,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   double bb = 0.0, prev = INFINITY, relres = INFINITY, scale = 1.0;
   bool resumable = false; // an inner PCG stopped cleanly and may continue
   for (;;) {
-    k_op64<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.br, P->d_S, P->d_c64, P->nr,
+    k_op64<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, brs, P->d_S, P->d_c64, P->nr,
                                                    P->nt, P->np, 0, r64, P->pitch, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 2);
     P->stats.launches += 2;
@@ -635,7 +682,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
       CTRY(cudaMemsetAsync(p1, 0, v4, s));
       CTRY(cudaMemsetAsync(q, 0, v4, s));
       k_start<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4, (double)P->n, inner_tol, inner_maxit, 0,
-                              1.0);
+                              1.0, nullptr);
       P->stats.launches += 4;
     }
     scale = new_scale;
@@ -655,6 +702,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     n_outer++;
   }
   k_unpad<<<gn, kAuxThreads, 0, s>>>(x64, P->pitch, io.phi, P->np, P->R, P->np);
+  gauge_phi(P, io.phi, P->d_part, P->d_sums + 6, s);
   P->stats.launches += 1;
   CTRY(cudaGetLastError());
   if (io.phi_host)
@@ -754,16 +802,31 @@ int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double 
   TRY(stage_io(P, br, const_cast<double *>(phi), B, true, io));
   const double *d_br = br ? io.br : P->d_br_last;
   cudaStream_t s = P->stream;
+  if (br && P->closed) {
+    // the inner face carries the balanced Br, the one a solve uses
+    prepare_br(P, io.br, P->d_br_tmp, P->d_part, P->d_sums + 6, s);
+    d_br = P->d_br_tmp;
+  }
   k_pole_avg<kAuxThreads><<<2 * P->nr, kAuxThreads, 0, s>>>(io.phi, P->nr, P->nt, P->np,
                                                             P->d_poles);
-  FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd};
+  FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd, P->closed ? 1 : 0};
   const size_t tot = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
-  k_field<<<aux_grid(P, tot), kAuxThreads, 0, s>>>(io.phi, d_br, P->d_poles, T, P->nr, P->nt, P->np,
-                                                    io.B);
+  const int gf = (int)std::min<size_t>(P->R, (size_t)8 * P->nsm);
+  k_field<<<gf, kFieldThreads, 0, s>>>(io.phi, d_br, P->d_poles, T, P->nr, P->nt, P->np, io.B);
   P->stats.launches = 2;
   CTRY(cudaGetLastError());
   if (io.B_host) CTRY(cudaMemcpyAsync(B, io.B, tot * sizeof(double), cudaMemcpyDeviceToHost, s));
   CTRY(cudaStreamSynchronize(s));
+  return POT3D_OK;
+}
+
+int pot3d_get_history(const pot3d_plan_t *plan, double *relres, int cap, int *n) {
+  if (!plan || !relres || cap < 0 || !n) return fail(POT3D_ERR_INVALID_ARG);
+  const Plan *P = reinterpret_cast<const Plan *>(plan);
+  if (!P->d_hist || P->hist_n <= 0) return fail(POT3D_ERR_INVALID_ARG);
+  const int m = std::min(cap, P->hist_n);
+  if (m > 0) CTRY(cudaMemcpy(relres, P->d_hist, sizeof(double) * m, cudaMemcpyDeviceToHost));
+  *n = m;
   return POT3D_OK;
 }
 
@@ -798,13 +861,19 @@ int pot3d_residual(pot3d_plan_t *plan, const double *br, const double *phi, doub
   Io io;
   TRY(stage_io(P, br, const_cast<double *>(phi), nullptr, true, io));
   cudaStream_t s = P->stream;
+  const double *brs = io.br;
+  if (P->closed) {
+    // the balanced Br, the one a solve uses
+    prepare_br(P, io.br, P->d_br_tmp, P->d_part, P->d_sums + 6, s);
+    brs = P->d_br_tmp;
+  }
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = aux_grid(P, n0);
-  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(io.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,
+  k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(brs, P->d_S, P->d_c64, P->nr, P->nt, P->np,
                                                    P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gb, P->d_sums);
   const int g = aux_grid(P, P->n);
-  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, io.br, P->d_S, P->d_c64, P->nr,
+  k_op64<kAuxThreads><<<g, kAuxThreads, 0, s>>>(io.phi, P->np, brs, P->d_S, P->d_c64, P->nr,
                                                 P->nt, P->np, 0, nullptr, P->np, P->d_part);
   k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, g, P->d_sums + 2);
   CTRY(cudaGetLastError());

@@ -29,7 +29,12 @@ KLaunch update_launcher(int ai);
 // resident blocks per SM of arithmetic ai's update kernel (0: unknown)
 int update_occupancy(int ai);
 
-constexpr int kUpdThreads = 256;
-constexpr int kUpdSegBytes = 2560; // bytes of r (and of q) per warp stage
+// Update kernel configurations per arithmetic: threads per block, bytes of
+// r (and of q) per warp stage, stages per warp.  The FP64 kernel is bound by
+// the FP64 unit; the HBM-bound ones keep more segments in flight.
+constexpr int kUpdSegBytes = 2560;
+constexpr int kUpdThreadsF64 = 256, kUpdStagesF64 = 2;
+constexpr int kUpdThreadsDF = 128, kUpdStagesDF = 4;
+constexpr int kUpdThreadsF32 = 128, kUpdStagesF32 = 5;
 
 } // namespace pot3d

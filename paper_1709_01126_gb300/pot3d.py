@@ -34,6 +34,7 @@ POT3D_OUTER_CLOSED_WALL = 1
 POT3D_POLE_AVERAGE = 0
 
 PRECISIONS = {"fp64": POT3D_PREC_FP64, "df": POT3D_PREC_FP64_DF, "mixed": POT3D_PREC_MIXED}
+OUTER = {"source": POT3D_OUTER_SOURCE_SURFACE, "closed": POT3D_OUTER_CLOSED_WALL}
 
 
 class pot3d_grid_t(ctypes.Structure):
@@ -51,7 +52,8 @@ class pot3d_opts_t(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("use_x0", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("mixed_restart", ctypes.c_int), ("verify", ctypes.c_int)]
+                ("mixed_restart", ctypes.c_int), ("verify", ctypes.c_int),
+                ("history", ctypes.c_int)]
 
 
 POT3D_FLAG_ABOVE_TOL = 1
@@ -77,7 +79,7 @@ EXPORTS = ["pot3d_plan", "pot3d_autotune", "pot3d_variant_info", "pot3d_set_deco
            "pot3d_batch_set_stream", "pot3d_batch_set_opts", "pot3d_batch_bytes_needed",
            "pot3d_batch_submit", "pot3d_batch_step", "pot3d_batch_poll", "pot3d_batch_info",
            "pot3d_last_error", "pot3d_strerror", "pot3d_selftest_wait", "pot3d_probe_fp64_fma",
-           "pot3d_test_freeze_poll"]
+           "pot3d_test_freeze_poll", "pot3d_get_history"]
 
 _lib = None
 
@@ -175,6 +177,7 @@ def load(build_if_missing: bool = False):
     L.pot3d_probe_fp64_fma.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
     L.pot3d_test_freeze_poll.argtypes = [P, I]
+    L.pot3d_get_history.argtypes = [P, D, I, ctypes.POINTER(I)]
     L.pot3d_last_error.argtypes = []
     L.pot3d_strerror.argtypes = [I]
     L.pot3d_strerror.restype = ctypes.c_char_p
@@ -222,7 +225,7 @@ class Plan:
     (PyTorch's allocator) handed to pot3d_set_workspace."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, precision="fp64", r_faces=None,
-                 t_faces=None, torch_workspace=False, **opts):
+                 t_faces=None, torch_workspace=False, outer="source", **opts):
         L = load()
         self._rf = None if r_faces is None else np.ascontiguousarray(r_faces, dtype=np.float64)
         self._tf = None if t_faces is None else np.ascontiguousarray(t_faces, dtype=np.float64)
@@ -232,13 +235,14 @@ class Plan:
                          None if self._tf is None else self._tf.ctypes.data_as(
                              ctypes.POINTER(ctypes.c_double)),
                          PRECISIONS.get(precision, precision))
-        bc = pot3d_bc_t(POT3D_OUTER_SOURCE_SURFACE, POT3D_POLE_AVERAGE)
+        bc = pot3d_bc_t(OUTER.get(outer, outer), POT3D_POLE_AVERAGE)
         h = L.pot3d_plan(ctypes.byref(g), ctypes.byref(bc))
         if not h:
             raise Pot3dError(L.pot3d_last_error(), "pot3d_plan")
         self.h = h
         self.nr, self.nt, self.np = int(nr), int(nt), int(np_)
         self.precision = precision
+        self.outer = outer
         self._ws = None
         if opts:
             self.set_opts(**opts)
@@ -267,9 +271,10 @@ class Plan:
             pass
 
     def set_opts(self, max_iters=0, use_x0=0, chunk=0, use_graphs=0, time_kernels=0,
-                 inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0):
+                 inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0, history=0):
         o = pot3d_opts_t(int(max_iters), int(use_x0), int(chunk), int(use_graphs), int(time_kernels),
-                         float(inner_tol), int(max_outer), int(mixed_restart), int(verify))
+                         float(inner_tol), int(max_outer), int(mixed_restart), int(verify),
+                         int(history))
         _check(load().pot3d_set_opts(self.h, ctypes.byref(o)), "pot3d_set_opts")
 
     def set_stream(self, stream_handle):
@@ -353,6 +358,16 @@ class Plan:
             return r.value
         return rc, r.value
 
+    def history(self):
+        """pot3d_get_history: the residual history of the last solve run with
+        history=1, as a numpy array (k = 0 .. iters)."""
+        cap = 1 << 22
+        buf = np.zeros(cap)
+        n = ctypes.c_int(0)
+        _check(load().pot3d_get_history(self.h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        cap, ctypes.byref(n)), "pot3d_get_history")
+        return buf[: n.value].copy()
+
     def field_sizes(self):
         nr, nt, np_ = self.shape
         return ((nr + 1) * nt * np_, nr * (nt + 1) * np_, nr * nt * np_)
@@ -370,7 +385,7 @@ class Batch:
         self.h = h
         self.max_slots = int(max_slots)
         o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer),
-                         int(mixed_restart), 0)
+                         int(mixed_restart), 0, 0)
         _check(L.pot3d_batch_set_opts(h, ctypes.byref(o)), "pot3d_batch_set_opts")
 
     def close(self):

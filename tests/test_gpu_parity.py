@@ -361,3 +361,26 @@ def test_verify_stops_on_true_residual(p3, oracle_mod, prec, tol):
         assert st["outer_iters"] == 0 and it == it0
     elif t0 > tol * 1.001:
         assert st["outer_iters"] >= 1 and it > it0
+
+
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-9), ("df", 1e-6)])
+def test_residual_history_matches_oracle(p3, oracle_mod, prec, bound):
+    """opts.history: the recurrence residual ||r_k|| / ||b|| of every
+    iteration, against the oracle's own history of the same solve."""
+    shape, ratio = (17, 35, 129), 1.02
+    br = make_br("bip", 35, 129)
+    g = oracle_mod.Grid(*shape, ratio=ratio)
+    _, it_ref, st, h_ref = g.pcg(g.rhs(br), 1e-12, history=True)
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec, history=1)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(dev(br), 1e-12, phi)
+    h = plan.history()
+    assert len(h) == it + 1 and h[0] == 1.0 and h[-1] <= 1e-12 < h[-2]
+    m = min(len(h), len(h_ref))
+    dev_rel = np.abs(h[:m] - h_ref[:m]) / h_ref[:m]
+    assert dev_rel.max() <= bound, dev_rel.max()
+    plan.set_opts()  # history off: nothing recorded
+    plan.solve(dev(br), 1e-12, phi)
+    with pytest.raises(p3.Pot3dError):
+        plan.history()
+    plan.close()
