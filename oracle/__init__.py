@@ -11,7 +11,9 @@ field code, written step by step from the paper:
   average.
 - Sec. 2.2 (finite-difference stencil) and Eq. 4: the 7-point operator, in
   its symmetric volume-weighted form with the r^2 metric factors restored.
-- Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1).
+- Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1); as the stronger
+  preconditioner Sec. 6 asks for, radial-line Jacobi (one tridiagonal solve
+  per (theta, phi) column).
 
 The wrapper below only marshals numpy arrays into the C routines.
 """
@@ -66,6 +68,8 @@ def _load():
             lib.orc_csr.argtypes = [i, i, i, _dp, _dp, _lp, _lp, _dp]
             lib.orc_csr.restype = ctypes.c_long
             lib.orc_set_outer.argtypes = [i]
+            lib.orc_set_precond.argtypes = [i]
+            lib.orc_precond.argtypes = [i, i, i, _dp, _dp, _dp, _dp]
             lib.orc_balance_br.argtypes = [i, i, i, _dp, _dp, _dp, _dp]
             lib.orc_remove_mean.argtypes = [ctypes.c_long, _dp]
             lib.orc_remove_mean.restype = None
@@ -89,6 +93,7 @@ def get_threads() -> int:
 
 
 OUTER = {"source": 0, "closed": 1}
+PRECOND = {"jacobi": 0, "rline": 1}
 
 
 class Grid:
@@ -97,12 +102,14 @@ class Grid:
     (the outer boundary), geometric with cell-width ratio ``ratio`` (1 =
     uniform) unless ``r_faces`` is given; theta faces are uniform unless
     ``t_faces`` is given.  ``outer``: "source" (source surface, Phi = 0 at r1)
-    or "closed" (closed wall, Br = 0 at r1), Sec. 2.1."""
+    or "closed" (closed wall, Br = 0 at r1), Sec. 2.1.  ``precond``: "jacobi"
+    (diagonal scaling, PC1 of Sec. 2.3) or "rline" (radial-line Jacobi)."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
-                 outer="source"):
+                 outer="source", precond="jacobi"):
         self.nr, self.nt, self.np = int(nr), int(nt), int(np_)
         self.outer = outer
+        self.precond = precond
         lib = _load()
         if r_faces is None:
             rf = np.empty(self.nr + 1)
@@ -141,6 +148,7 @@ class Grid:
 
     def _dims(self):
         _load().orc_set_outer(OUTER[self.outer])
+        _load().orc_set_precond(PRECOND[self.precond])
         return self.nr, self.nt, self.np, _p(self.rf), _p(self.tf)
 
     # -- operator (Sec. 2.2, Eq. 4) --------------------------------------
@@ -161,6 +169,13 @@ class Grid:
         cp = np.empty((self.nr, self.nt))
         _load().orc_coeffs(*self._dims(), _p(cr), _p(ct), _p(cp))
         return cr, ct, cp
+
+    def apply_precond(self, r: np.ndarray) -> np.ndarray:
+        """z = M^-1 r with this grid's preconditioner."""
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(self.shape)
+        z = np.empty_like(r)
+        _load().orc_precond(*self._dims(), _p(r), _p(z))
+        return z
 
     def rhs(self, br: np.ndarray) -> np.ndarray:
         br = np.ascontiguousarray(br, dtype=np.float64).reshape(self.nt, self.np)

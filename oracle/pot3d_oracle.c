@@ -72,6 +72,19 @@ typedef struct {
 
 static int g_threads = 0;
 static int g_outer_closed = 0; /* 0: source surface Phi = 0; 1: closed wall Br = 0 */
+static int g_precond = 0;      /* 0: point Jacobi (PC1); 1: radial-line Jacobi */
+
+/* Preconditioner of orc_pcg: 0 = diagonal scaling (PC1 of Sec. 2.3);
+ * 1 = radial-line Jacobi: M is the part of L that couples cells of the same
+ * (theta, phi) column, i.e. the full diagonal and the two radial
+ * neighbours, and z = M^-1 r is one tridiagonal solve per column (a
+ * preconditioner of the kind Sec. 6 asks for: stronger than diagonal
+ * scaling, yet every column is independent). */
+int orc_set_precond(int kind) {
+  if (kind != 0 && kind != 1) return 3;
+  g_precond = kind;
+  return 0;
+}
 
 /* Outer boundary condition used by every later call: 0 = source surface,
  * 1 = closed wall. */
@@ -231,6 +244,54 @@ static void op_apply(const orc_op *op, const double *x, double *y) {
   }
 }
 
+/* ------------------------------------------------------ preconditioner */
+
+/* z = M^-1 r.  PC1: z = r / diag.  Radial lines: for each column (j, k) the
+ * tridiagonal system with diagonal diag[i][j], sub- and super-diagonal
+ * -cr[i][j] between cells i and i+1, solved by Gaussian elimination without
+ * pivoting (the Thomas algorithm: forward elimination, back substitution;
+ * the matrix is symmetric and diagonally dominant, so no pivoting is
+ * needed). */
+static void precond_apply(const orc_op *op, const double *r, double *z) {
+  const int nr = op->nr, nt = op->nt, np = op->np;
+  const long plane = (long)nt * np;
+  if (g_precond == 0) {
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)nr * plane; c++) z[c] = r[c] / op->diag[c / np];
+    return;
+  }
+#pragma omp parallel
+  {
+    double *cp = malloc(sizeof(double) * nr); /* modified super-diagonal */
+    double *dp = malloc(sizeof(double) * nr); /* modified right-hand side */
+#pragma omp for schedule(static)
+    for (long col = 0; col < plane; col++) {
+      const int j = (int)(col / np);
+      /* row i: a_i z_{i-1} + b_i z_i + c_i z_{i+1} = r_i with
+         a_i = -cr[i-1][j], b_i = diag[i][j], c_i = -cr[i][j] */
+      for (int i = 0; i < nr; i++) {
+        const double a = (i > 0) ? -op->cr[(i - 1) * nt + j] : 0.0;
+        const double b = op->diag[i * nt + j];
+        const double c = (i < nr - 1) ? -op->cr[i * nt + j] : 0.0;
+        const double ri = r[(long)i * plane + col];
+        if (i == 0) {
+          cp[0] = c / b;
+          dp[0] = ri / b;
+        } else {
+          const double m = b - a * cp[i - 1];
+          cp[i] = c / m;
+          dp[i] = (ri - a * dp[i - 1]) / m;
+        }
+      }
+      z[(long)(nr - 1) * plane + col] = dp[nr - 1];
+      for (int i = nr - 2; i >= 0; i--)
+        z[(long)i * plane + col] = dp[i] - cp[i] * z[(long)(i + 1) * plane + col];
+    }
+    free(cp);
+    free(dp);
+  }
+}
+
 /* ------------------------------------------------------ vector helpers */
 
 static double dot(long n, const double *a, const double *b) {
@@ -265,6 +326,18 @@ int orc_apply(int nr, int nt, int np, const double *rf, const double *tf, const 
   int st = op_build(&op, nr, nt, np, rf, tf);
   if (st) return st;
   op_apply(&op, x, y);
+  op_free(&op);
+  return ORC_OK;
+}
+
+/* z = M^-1 r with the preconditioner of orc_set_precond (exposed for the
+ * tests). */
+int orc_precond(int nr, int nt, int np, const double *rf, const double *tf, const double *r,
+                double *z) {
+  orc_op op;
+  int st = op_build(&op, nr, nt, np, rf, tf);
+  if (st) return st;
+  precond_apply(&op, r, z);
   op_free(&op);
   return ORC_OK;
 }
@@ -346,9 +419,9 @@ int orc_rhs(int nr, int nt, int np, const double *rf, const double *tf, const do
   return ORC_OK;
 }
 
-/* Textbook preconditioned conjugate gradient with point-Jacobi (diagonal
- * scaling) preconditioner, PC1 of Sec. 2.3 (Saad, Iterative Methods,
- * Algorithm 9.1).  x holds the initial guess when x0_given != 0, else it is
+/* Textbook preconditioned conjugate gradient (Saad, Iterative Methods,
+ * Algorithm 9.1) with the preconditioner of orc_set_precond: point Jacobi
+ * (diagonal scaling, PC1 of Sec. 2.3) by default, or radial-line Jacobi.  x holds the initial guess when x0_given != 0, else it is
  * zeroed.  Stops after iteration k when ||r_k||_2 / ||b||_2 <= tol.
  * relres (optional, length maxit+1) receives ||r_k||/||b|| for k = 0..iters.
  * Returns ORC_OK, ORC_NOT_CONVERGED (iters == maxit, x = last iterate) or
@@ -378,10 +451,8 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
     for (long c = 0; c < n; c++) { x[c] = 0.0; r[c] = b[c]; }
   }
   const double bnorm = sqrt(dot(n, b, b));
-  const int np_ = np;
-  /* z_0 = D^-1 r_0 */
-#pragma omp parallel for schedule(static)
-  for (long c = 0; c < n; c++) z[c] = r[c] / op.diag[c / np_];
+  /* z_0 = M^-1 r_0 */
+  precond_apply(&op, r, z);
   /* p_0 = z_0 */
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < n; c++) p[c] = z[c];
@@ -409,9 +480,8 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
     rn = sqrt(dot(n, r, r));
     if (relres) relres[k] = rn / bnorm;
     if (rn / bnorm <= tol) { status = ORC_OK; break; }
-    /* z = D^-1 r */
-#pragma omp parallel for schedule(static)
-    for (long c = 0; c < n; c++) z[c] = r[c] / op.diag[c / np_];
+    /* z = M^-1 r */
+    precond_apply(&op, r, z);
     /* beta = (r_new . z_new) / (r_old . z_old) */
     double rho_new = dot(n, r, z);
     double beta = rho_new / rho;
