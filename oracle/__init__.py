@@ -12,8 +12,9 @@ field code, written step by step from the paper:
 - Sec. 2.2 (finite-difference stencil) and Eq. 4: the 7-point operator, in
   its symmetric volume-weighted form with the r^2 metric factors restored.
 - Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1); as the stronger
-  preconditioner Sec. 6 asks for, radial-line Jacobi (one tridiagonal solve
-  per (theta, phi) column).
+  preconditioners Sec. 6 asks for, radial-line Jacobi (one tridiagonal solve
+  per (theta, phi) column) and phi-line Jacobi (one cyclic tridiagonal solve
+  per (r, theta) ring).
 
 The wrapper below only marshals numpy arrays into the C routines.
 """
@@ -93,7 +94,7 @@ def get_threads() -> int:
 
 
 OUTER = {"source": 0, "closed": 1}
-PRECOND = {"jacobi": 0, "rline": 1}
+PRECOND = {"jacobi": 0, "rline": 1, "philine": 2}
 
 
 class Grid:
@@ -103,7 +104,8 @@ class Grid:
     uniform) unless ``r_faces`` is given; theta faces are uniform unless
     ``t_faces`` is given.  ``outer``: "source" (source surface, Phi = 0 at r1)
     or "closed" (closed wall, Br = 0 at r1), Sec. 2.1.  ``precond``: "jacobi"
-    (diagonal scaling, PC1 of Sec. 2.3) or "rline" (radial-line Jacobi)."""
+    (diagonal scaling, PC1 of Sec. 2.3), "rline" (radial-line Jacobi) or
+    "philine" (phi-line Jacobi: one cyclic tridiagonal solve per ring)."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
                  outer="source", precond="jacobi"):

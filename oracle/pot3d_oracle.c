@@ -72,16 +72,19 @@ typedef struct {
 
 static int g_threads = 0;
 static int g_outer_closed = 0; /* 0: source surface Phi = 0; 1: closed wall Br = 0 */
-static int g_precond = 0;      /* 0: point Jacobi (PC1); 1: radial-line Jacobi */
+static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi lines */
 
-/* Preconditioner of orc_pcg: 0 = diagonal scaling (PC1 of Sec. 2.3);
- * 1 = radial-line Jacobi: M is the part of L that couples cells of the same
- * (theta, phi) column, i.e. the full diagonal and the two radial
- * neighbours, and z = M^-1 r is one tridiagonal solve per column (a
- * preconditioner of the kind Sec. 6 asks for: stronger than diagonal
- * scaling, yet every column is independent). */
+/* Preconditioner of orc_pcg (line preconditioners are of the kind Sec. 6
+ * asks for: stronger than diagonal scaling, yet every line independent):
+ *   0 = diagonal scaling (PC1 of Sec. 2.3);
+ *   1 = radial-line Jacobi: M is the part of L that couples cells of one
+ *       (theta, phi) column (the full diagonal and the two radial
+ *       neighbours); z = M^-1 r is one tridiagonal solve per column;
+ *   2 = phi-line Jacobi: M is the part of L that couples cells of one
+ *       (r, theta) ring (the full diagonal and the two periodic phi
+ *       neighbours); z = M^-1 r is one cyclic tridiagonal solve per ring. */
 int orc_set_precond(int kind) {
-  if (kind != 0 && kind != 1) return 3;
+  if (kind < 0 || kind > 2) return 3;
   g_precond = kind;
   return 0;
 }
@@ -252,12 +255,78 @@ static void op_apply(const orc_op *op, const double *x, double *y) {
  * pivoting (the Thomas algorithm: forward elimination, back substitution;
  * the matrix is symmetric and diagonally dominant, so no pivoting is
  * needed). */
+/* Tridiagonal solve (Thomas algorithm) of rows i = 0..n-1:
+ * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i, a_0 and c_{n-1} unused;
+ * cp, dp: n doubles of workspace. */
+static void thomas(int n, const double *a, const double *b, const double *c, const double *d,
+                   double *x, double *cp, double *dp) {
+  cp[0] = c[0] / b[0];
+  dp[0] = d[0] / b[0];
+  for (int i = 1; i < n; i++) {
+    const double m = b[i] - a[i] * cp[i - 1];
+    cp[i] = c[i] / m;
+    dp[i] = (d[i] - a[i] * dp[i - 1]) / m;
+  }
+  x[n - 1] = dp[n - 1];
+  for (int i = n - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
+}
+
+/* Cyclic tridiagonal solve, diagonal dg, both off-diagonals (including the
+ * two corners that close the ring) equal to off: the Sherman-Morrison
+ * formula around one tridiagonal matrix B (A = B + u v^T with
+ * u = (g, 0, .., 0, off), v = (1, 0, .., 0, off / g), g = -dg), two Thomas
+ * solves B y = d and B w = u, then x = y - (v.y) / (1 + v.w) w.
+ * n >= 3; work: 7 n doubles. */
+static void cyclic_solve(int n, double dg, double off, const double *d, double *x, double *work) {
+  double *a = work, *b = work + n, *c = work + 2 * n, *u = work + 3 * n, *w = work + 4 * n;
+  double *cp = work + 5 * n, *dp = work + 6 * n;
+  const double g = -dg;
+  for (int i = 0; i < n; i++) {
+    a[i] = off;
+    b[i] = dg;
+    c[i] = off;
+    u[i] = 0.0;
+  }
+  b[0] = dg - g;
+  b[n - 1] = dg - off * off / g;
+  u[0] = g;
+  u[n - 1] = off;
+  thomas(n, a, b, c, d, x, cp, dp);
+  thomas(n, a, b, c, u, w, cp, dp);
+  const double vy = x[0] + (off / g) * x[n - 1];
+  const double vw = w[0] + (off / g) * w[n - 1];
+  const double f = vy / (1.0 + vw);
+  for (int i = 0; i < n; i++) x[i] -= f * w[i];
+}
+
 static void precond_apply(const orc_op *op, const double *r, double *z) {
   const int nr = op->nr, nt = op->nt, np = op->np;
   const long plane = (long)nt * np;
   if (g_precond == 0) {
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < (long)nr * plane; c++) z[c] = r[c] / op->diag[c / np];
+    return;
+  }
+  if (g_precond == 2) {
+#pragma omp parallel
+    {
+      double *work = malloc(sizeof(double) * 7 * (np > 3 ? np : 3));
+#pragma omp for schedule(static)
+      for (long row = 0; row < (long)nr * nt; row++) {
+        const double dg = op->diag[row], off = -op->cp[row];
+        const double *rr = r + row * np;
+        double *zz = z + row * np;
+        if (np == 2) {
+          /* both phi faces couple to the one other cell: [[dg, 2 off], [2 off, dg]] */
+          const double det = dg * dg - 4.0 * off * off;
+          zz[0] = (dg * rr[0] - 2.0 * off * rr[1]) / det;
+          zz[1] = (dg * rr[1] - 2.0 * off * rr[0]) / det;
+        } else {
+          cyclic_solve(np, dg, off, rr, zz, work);
+        }
+      }
+      free(work);
+    }
     return;
   }
 #pragma omp parallel
