@@ -63,6 +63,14 @@ extern "C" {
                              /* operation in double-float arithmetic on FP32 units  */
 #define POT3D_PREC_MIXED 2   /* FP32 inner PCG inside FP64 iterative refinement     */
 
+/* ---- preconditioner of the PCG iteration ------------------------------ */
+#define POT3D_PC_JACOBI 0   /* diagonal scaling z = D^-1 r (PC1, Sec. 2.3)             */
+#define POT3D_PC_PHI_LINE 1 /* phi-line Jacobi: z = T^-1 r with T the part of L that
+                               couples the cells of one (r, theta) ring (diagonal and
+                               both phi neighbours, periodic): a cyclic tridiagonal
+                               solve per ring, the stronger line preconditioner of
+                               the kind Sec. 6 calls for.  FP64 and MIXED plans       */
+
 /* ---- boundary conditions (Sec. 2.1) ---------------------------------- */
 #define POT3D_OUTER_SOURCE_SURFACE 0 /* Phi = 0 at r = r1                              */
 #define POT3D_OUTER_CLOSED_WALL 1    /* Br = dPhi/dr = 0 at r = r1.  The operator is then
@@ -120,6 +128,9 @@ typedef struct {
                          most 10 restarts, within max_iters in total).  stats
                          report the FP64 residual and the restarts (outer_iters).
                          MIXED always stops on the FP64 residual.                */
+  int precond;        /* POT3D_PC_*: the preconditioner (POT3D_PC_PHI_LINE with FP64
+                         or MIXED plans, and in single solves only: a FP64_DF plan
+                         or a batch submission returns POT3D_ERR_UNSUPPORTED)   */
   int history;        /* FP64 and FP64_DF: 1 = record the recurrence residual
                          ||r_k|| / ||b|| of every iteration k = 0 .. iters of the
                          next solves (with verify: of the last restart), read back

@@ -149,6 +149,16 @@ struct PF64 {
   static __device__ __forceinline__ void d_merge(dacc &d, const dacc &s) { d.v += s.v; }
   static __device__ __forceinline__ val from_double(double x) { return x; }
   static __device__ __forceinline__ double to_double(val v) { return v; }
+  // scalar helpers of the phi-line ring solve
+  static __device__ __forceinline__ val one() { return 1.0; }
+  static __device__ __forceinline__ val mul(val a, val b) { return a * b; }
+  static __device__ __forceinline__ val sub(val a, val b) { return a - b; }
+  static __device__ __forceinline__ val div(val a, val b) { return a / b; }
+  static __device__ __forceinline__ val shfl_up(val v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+  static __device__ __forceinline__ val shfl_down(val v, int d) {
+    return __shfl_down_sync(0xffffffffu, v, d);
+  }
+  static __device__ __forceinline__ val shfl_idx(val v, int l) { return __shfl_sync(0xffffffffu, v, l); }
   // 16-byte vector of kVec elements
   static __device__ __forceinline__ void ldv(const st *p, val (&v)[kVec]) {
     double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
@@ -248,6 +258,16 @@ struct PF32 {
   static __device__ __forceinline__ void d_merge(dacc &d, const dacc &s) { cacc_add(d, s.s, s.c); }
   static __device__ __forceinline__ val from_double(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ double to_double(val v) { return (double)v; }
+  // scalar helpers of the phi-line ring solve
+  static __device__ __forceinline__ val one() { return 1.f; }
+  static __device__ __forceinline__ val mul(val a, val b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ val sub(val a, val b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ val div(val a, val b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ val shfl_up(val v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+  static __device__ __forceinline__ val shfl_down(val v, int d) {
+    return __shfl_down_sync(0xffffffffu, v, d);
+  }
+  static __device__ __forceinline__ val shfl_idx(val v, int l) { return __shfl_sync(0xffffffffu, v, l); }
   static __device__ __forceinline__ void ldv(const st *p, val (&v)[kVec]) {
     float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
     v[0] = t.x;

@@ -94,6 +94,11 @@ static __global__ void k_start(SolveState *st, const double *sums, double n0, do
   if (hist) hist[0] = relres;
 }
 
+// rho of the state from sums[1] (phi-line start: r . T^-1 r of r_0).
+static __global__ void k_set_rho(SolveState *st, const double *sums) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->rho = sums[1];
+}
+
 // Residual replacement of the refinement loop (reliable update): the inner
 // PCG stopped after iteration K; its correction was folded into x64, the
 // FP64 residual recomputed and scaled into r32 (sums: ||r32||^2 and
@@ -372,43 +377,37 @@ struct FieldTabs {
 };
 
 // B = grad Phi on the staggered faces; see the header for the layout.
-// A block takes one (i, j) row of cells at a time (grid-stride over the
-// rows), its threads the phi index k, and writes every face the row owns:
+// One thread per cell (i, j, k) in C order writes every face the cell owns:
 // the radial face below it (i), the colatitude face north of it (j) and the
-// phi face after each cell; the last radial layer also writes the outer
-// face and the last colatitude row the south pole face.  Phi is read once
-// from HBM (the neighbouring rows come from L2) and every write is
-// coalesced; no 64-bit division in the index arithmetic.
-constexpr int kFieldThreads = 128;
+// phi face after it; the last radial layer also writes the outer face and
+// the last colatitude row the south pole face.  Consecutive threads take
+// consecutive k, so every read of Phi (the cell, its lower radial and
+// northern neighbours, its phi successor) and every write is coalesced, and
+// Phi comes from HBM once (the neighbouring rows were read just before and
+// sit in L2).  Index arithmetic in 32 bits (the host checks n < 2^31).
+constexpr int kFieldThreads = 256;
 static __global__ void __launch_bounds__(kFieldThreads)
     k_field(const double *__restrict__ phi, const double *__restrict__ br,
             const double *__restrict__ poles, FieldTabs T, int nr, int nt, int np,
             double *__restrict__ B) {
-  const size_t rplane = (size_t)nt * np;          // one radial layer of Phi / Br faces
+  const unsigned n = (unsigned)nr * nt * np, rplane = (unsigned)nt * np;
   double *const Bt = B + (size_t)(nr + 1) * rplane; // colatitude faces [nr][nt+1][np]
   double *const Bp = Bt + (size_t)nr * (nt + 1) * np;
-  for (int q = blockIdx.x; q < nr * nt; q += gridDim.x) {
-    const int i = q / nt, j = q - i * nt;
-    const double *ph = phi + (size_t)q * np;
-    double *br_o = B + (size_t)q * np;                            // radial face i
-    double *bt_o = Bt + ((size_t)i * (nt + 1) + j) * np;          // colatitude face j
-    double *bp_o = Bp + (size_t)q * np;
-    const double ir = T.irc[i], irs = T.irs[i], itj = T.its[j], isd = T.isd[j];
-    for (int k = threadIdx.x; k < np; k += kFieldThreads) {
-      const double v = ph[k];
-      // ghost chosen so that dPhi/dr = Br on the inner face (Eq. 2)
-      br_o[k] = (i == 0) ? br[(size_t)j * np + k] : (v - ph[(ptrdiff_t)k - (ptrdiff_t)rplane]) * irs;
-      // ghost 2 avg - Phi across the north pole: the face value is the
-      // ring's phi-average (Eq. 3)
-      bt_o[k] = (j == 0) ? 2.0 * (v - poles[2 * i]) * T.its[0] * ir : (v - ph[k - np]) * itj * ir;
-      const int kp = (k + 1 == np) ? 0 : k + 1;
-      bp_o[k] = (ph[kp] - v) * ir * isd;
-      if (i == nr - 1) {
-        // source surface: ghost -Phi (Phi = 0 there); closed wall: ghost Phi
-        br_o[(size_t)rplane + k] = T.closed ? 0.0 : (-2.0 * v) * T.irs[nr];
-      }
-      if (j == nt - 1) bt_o[np + k] = 2.0 * (poles[2 * i + 1] - v) * T.its[nt] * ir;
-    }
+  for (unsigned e = blockIdx.x * kFieldThreads + threadIdx.x; e < n;
+       e += gridDim.x * kFieldThreads) {
+    const unsigned q = e / np, k = e - q * np, i = q / nt, j = q - i * nt;
+    const double v = phi[e], ir = T.irc[i];
+    // ghost chosen so that dPhi/dr = Br on the inner face (Eq. 2)
+    B[e] = (i == 0) ? br[(size_t)j * np + k] : (v - phi[e - rplane]) * T.irs[i];
+    // ghost 2 avg - Phi across the north pole: the face value is the ring's
+    // phi-average (Eq. 3)
+    const size_t ot = ((size_t)i * (nt + 1) + j) * np + k;
+    Bt[ot] = (j == 0) ? 2.0 * (v - poles[2 * i]) * T.its[0] * ir : (v - phi[e - np]) * T.its[j] * ir;
+    const unsigned ep = (k + 1 == (unsigned)np) ? e + 1 - np : e + 1;
+    Bp[e] = (phi[ep] - v) * ir * T.isd[j];
+    // source surface: ghost -Phi (Phi = 0 there); closed wall: ghost Phi
+    if (i == (unsigned)nr - 1) B[e + rplane] = T.closed ? 0.0 : (-2.0 * v) * T.irs[nr];
+    if (j == (unsigned)nt - 1) Bt[ot + np] = 2.0 * (poles[2 * i + 1] - v) * T.its[nt] * ir;
   }
 }
 

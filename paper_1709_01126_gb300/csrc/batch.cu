@@ -418,6 +418,7 @@ int pot3d_batch_set_opts(pot3d_batch_t *batch, const pot3d_opts_t *o) {
   if (!batch || !o || o->inner_tol < 0 || !(o->inner_tol < 1.0) || o->max_outer < 0 ||
       o->max_iters < 0)
     return fail(POT3D_ERR_INVALID_ARG);
+  if (o->precond != POT3D_PC_JACOBI) return fail(POT3D_ERR_UNSUPPORTED); // diagonal scaling only
   reinterpret_cast<Batch *>(batch)->opts = *o;
   return POT3D_OK;
 }

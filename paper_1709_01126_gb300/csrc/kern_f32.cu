@@ -12,6 +12,9 @@ const MvVariant *mv_variants_f32(int *count) {
 }
 
 KLaunch update_launcher_f32() { return &up_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>; }
+KLineLaunch update_line_launcher_f32() {
+  return &up_line_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>;
+}
 int update_occupancy_f32() { return up_occupancy<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>(); }
 
 // Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
@@ -32,6 +35,13 @@ KLaunch update_launcher(int ai) {
   if (ai == 0) return update_launcher_f64();
   if (ai == 1) return update_launcher_df();
   return update_launcher_f32();
+}
+
+KLineLaunch update_line_launcher_f64();
+KLineLaunch update_line_launcher(int ai) {
+  if (ai == 0) return update_line_launcher_f64();
+  if (ai == 2) return update_line_launcher_f32();
+  return nullptr;
 }
 
 int update_occupancy(int ai) {

@@ -11,6 +11,9 @@ const MvVariant *mv_variants_f64(int *count) {
 }
 
 KLaunch update_launcher_f64() { return &up_launch<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>; }
+KLineLaunch update_line_launcher_f64() {
+  return &up_line_launch<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>;
+}
 int update_occupancy_f64() { return up_occupancy<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>(); }
 
 } // namespace pot3d

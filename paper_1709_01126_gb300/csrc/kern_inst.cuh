@@ -64,7 +64,29 @@ void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int gri
                cudaStream_t s) {
   using LY = UpLayout<NT, SEGB, STG>;
   up_setup<A, NT, SEGB, STG>();
-  k_update<A, NT, SEGB, STG><<<grid, NT, LY::BYTES, s>>>(probs, work, nwork);
+  k_update<A, NT, SEGB, STG><<<grid, NT, LY::BYTES, s>>>(probs, work, nwork, nullptr);
+}
+
+// Phi-line update: the stage layout plus one ring buffer of `pitch` values
+// per warp.  Returns 0, or -1 when the shared memory would exceed what a
+// block may use (the ring is too long for this configuration).
+template <class A, int NT, int SEGB, int STG>
+int up_line_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid, int pitch,
+                   double *setup_out, cudaStream_t s) {
+  using LY = UpLayout<NT, SEGB, STG>;
+  const size_t bytes = LY::BYTES + (size_t)(NT / 32) * pitch * sizeof(typename A::val);
+  static size_t set_to = 0;
+  if (bytes > set_to) {
+    if (bytes > 227 * 1024 ||
+        cudaFuncSetAttribute(k_update<A, NT, SEGB, STG, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    set_to = bytes;
+  }
+  k_update<A, NT, SEGB, STG, true><<<grid, NT, bytes, s>>>(probs, work, nwork, setup_out);
+  return 0;
 }
 
 // resident blocks of the update kernel per SM (0 if the query fails)

@@ -85,6 +85,8 @@ struct ProbDev {
   double *hist;       // residual history [hist_cap] (null: not recorded)
   int hist_cap;
   int pad2_;
+  void *w;            // phi-line preconditioner: w = D M^-1 r (null: PC1)
+  const void *lcoef;  // phi-line table [3][nr][ntp]: mu, mu / c, D mu / c
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -587,8 +589,98 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                : "memory");
 }
 
+// ------------------------------------------------------- phi-line solve
+// The phi-line preconditioner (one cyclic tridiagonal system per ring of
+// fixed (i, j): diagonal D, both phi couplings -c) has constant coefficients
+// along the ring, so it factors exactly as
+//   T = d - c (S + S^-1) = (c / mu) (1 - mu S)(1 - mu S^-1),
+// S the cyclic shift and mu + 1 / mu = d / c, 0 < mu < 1.  Hence
+//   T^-1 = (mu / c) F F^T,   F = (1 - mu S)^-1,
+// and F is a first-order recurrence around the ring, u_k = x_k + mu u_{k-1}
+// (indices mod n), whose periodic solution is exact: with u_{-1} the value
+// that closes the ring, u_{n-1} = mu^n u_{-1} + (the value reached from 0)
+// fixes u_{-1}.  F^T is the same recurrence run backwards.  A warp solves a
+// ring held in shared memory: every lane runs its contiguous chunk from a
+// zero carry, the chunk maps c -> mu^len c + s are composed across lanes by
+// a shuffle scan, the ring closure gives the carry into every chunk, and a
+// second pass applies the recurrence from the right carry.  Returns (in
+// acc) this lane's share of ||F x||^2; x is overwritten by F^T F x.
+template <class A>
+__device__ __forceinline__ typename A::val lane_pow(typename A::val mu, int e) {
+  typename A::val r = A::one(), b = mu;
+  while (e > 0) {
+    if (e & 1) r = A::mul(r, b);
+    b = A::mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+template <class A>
+__device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A::val mu,
+                                           typename A::dacc &acc, int lane) {
+  using val = typename A::val;
+  const int m = (n + 31) >> 5;
+  const int a = min(lane * m, n), b = min(a + m, n);
+  const val pm = lane_pow<A>(mu, b - a);
+  // ---- forward recurrence u_k = x_k + mu u_{k-1}
+  val t = A::zero();
+  for (int k = a; k < b; k++) t = A::fma(mu, t, x[k]);
+  val M = pm, S = t;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const val M2 = A::shfl_up(M, off), S2 = A::shfl_up(S, off);
+    if (lane >= off) {
+      S = A::fma(M, S2, S);
+      M = A::mul(M, M2);
+    }
+  }
+  val Sx = A::shfl_up(S, 1), Px = A::shfl_up(M, 1);
+  if (lane == 0) {
+    Sx = A::zero();
+    Px = A::one();
+  }
+  val total = A::shfl_idx(S, 31), mun = A::shfl_idx(M, 31);
+  t = A::fma(Px, A::div(total, A::sub(A::one(), mun)), Sx); // carry into this chunk
+  for (int k = a; k < b; k++) {
+    t = A::fma(mu, t, x[k]);
+    x[k] = t;
+    A::d_add(acc, t, t);
+  }
+  __syncwarp();
+  // ---- backward recurrence v_k = u_k + mu v_{k+1}
+  t = A::zero();
+  for (int k = b - 1; k >= a; k--) t = A::fma(mu, t, x[k]);
+  M = pm;
+  S = t;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const val M2 = A::shfl_down(M, off), S2 = A::shfl_down(S, off);
+    if (lane + off < 32) {
+      S = A::fma(M, S2, S);
+      M = A::mul(M, M2);
+    }
+  }
+  Sx = A::shfl_down(S, 1);
+  Px = A::shfl_down(M, 1);
+  if (lane == 31) {
+    Sx = A::zero();
+    Px = A::one();
+  }
+  total = A::shfl_idx(S, 0);
+  mun = A::shfl_idx(M, 0);
+  t = A::fma(Px, A::div(total, A::sub(A::one(), mun)), Sx);
+  for (int k = b - 1; k >= a; k--) {
+    t = A::fma(mu, t, x[k]);
+    x[k] = t;
+  }
+  __syncwarp();
+}
+
 // Shared memory of k_update: per warp STG stages of (r, q) segments of
-// SEGB bytes each, then STG mbarriers per warp.
+// SEGB bytes each, then STG mbarriers per warp; with the phi-line
+// preconditioner, then one ring buffer of `pitch` values per warp (sized at
+// launch).
 template <int NT, int SEGB, int STG>
 struct UpLayout {
   static constexpr int NW = NT / 32;
@@ -605,10 +697,18 @@ struct UpLayout {
 // before its first segment is awaited.  r -= alpha q is written back from
 // registers; per row s = sum r^2, then ||r||^2 += s and rho += D^-1 s.  The
 // last block closes the iteration.
-template <class A, int NT, int SEGB, int STG>
+//
+// LINE (phi-line preconditioner): the warp also keeps the updated ring in
+// its ring buffer and, at the ring's end, forms z = T^-1 r there
+// (ring_solve), accumulates rho = r.z = (mu / c) ||F r||^2 and writes
+// w = D z, the vector the next matvec reads in place of r.  setup_out
+// non-null (LINE only): alpha = 0 and no iteration is closed; the last
+// block writes ||r||^2 and rho to setup_out[0..1] (the start of a solve or
+// of a refinement step).
+template <class A, int NT, int SEGB, int STG, bool LINE = false>
 __global__ void __launch_bounds__(NT)
     k_update(const ProbDev *__restrict__ probs, const int2 *__restrict__ work,
-             const int *__restrict__ nwork_p) {
+             const int *__restrict__ nwork_p, double *setup_out) {
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
@@ -622,6 +722,8 @@ __global__ void __launch_bounds__(NT)
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, tid = threadIdx.x;
   st *wbuf = reinterpret_cast<st *>(smu + wy * LY::WARP_BYTES); // [stage][r|q][SEG]
   uint64_t *wbar = reinterpret_cast<uint64_t *>(smu + NW * LY::WARP_BYTES) + STG * wy;
+  val *ring = reinterpret_cast<val *>(smu + LY::BYTES); // [NW][pitch] when LINE
+  const bool setup = LINE && setup_out != nullptr;
   if (lane == 0) {
     for (int g = 0; g < STG; g++) mbar_init(&wbar[g], 1);
     mbar_fence_init();
@@ -633,7 +735,7 @@ __global__ void __launch_bounds__(NT)
     const int2 wi = work[w];
     const ProbDev &P = probs[wi.x];
     SolveState *stt = P.st;
-    if (ldcg(&stt->status) != ST_RUNNING) continue;
+    if (!setup && ldcg(&stt->status) != ST_RUNNING) continue;
     const int kit = ldcg(&stt->iter) + 1;
     const int t = wi.y;
     const int nt = P.nt, np = P.np, pitch = P.pitch, ntp = P.ntp;
@@ -643,8 +745,18 @@ __global__ void __launch_bounds__(NT)
     st *__restrict__ r = static_cast<st *>(P.r);
     const st *__restrict__ q = static_cast<const st *>(P.q);
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
-    const typename A::scal nalpha = A::scal_from(-ldcg(&stt->alpha[kit & 1]));
-    typename A::dacc arr = A::d_init(), arho = A::d_init(), s = A::d_init();
+    // phi-line table slabs: mu, mu / c, D mu / c
+    const coef *__restrict__ lc = static_cast<const coef *>(P.lcoef);
+    st *__restrict__ wv = static_cast<st *>(P.w);
+    val *xr = ring + (size_t)wy * pitch;
+    const size_t RT = (size_t)P.nr * ntp;
+    const typename A::scal nalpha =
+        A::scal_from(setup ? 0.0 : -ldcg(&stt->alpha[kit & 1]));
+    // per-row sums of r^2: one accumulator per vector element (independent
+    // dependency chains), merged at the end of the row
+    typename A::dacc arr = A::d_init(), arho = A::d_init(), s[V];
+#pragma unroll
+    for (int e = 0; e < V; e++) s[e] = A::d_init();
     const int nseg = (np + SEG - 1) / SEG;
     const int nrows_w = (row1 - row0 - wy + NW - 1) / NW;
     const int units = nrows_w > 0 ? nrows_w * nseg : 0;
@@ -690,10 +802,19 @@ __global__ void __launch_bounds__(NT)
     int issued = 0;
     for (; issued < min(units, STG - 1); issued++) issue(issued);
     int u = 0;
-    coef wrow{};
+    coef wrow{}, lmu{}, lgd{};
     for (; u < units; u++) {
       if (issued < units) issue(issued++);
-      if (cc.seg == 0) wrow = cf[(size_t)cc.i * ntp + cc.j]; // ahead of the wait
+      if (cc.seg == 0) { // ahead of the wait
+        const size_t rj = (size_t)cc.i * ntp + cc.j;
+        if constexpr (LINE) {
+          lmu = lc[rj];
+          wrow = lc[RT + rj];
+          lgd = lc[2 * RT + rj];
+        } else {
+          wrow = cf[rj];
+        }
+      }
       const uint32_t stg = (useq + u) % STG;
       if (!mbar_wait(&wbar[stg], ((useq + u) / STG) & 1u)) {
         bad = true;
@@ -713,15 +834,37 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
         for (int e = 0; e < V; e++) {
           rv[e] = A::fma(nalpha, qv[e], rv[e]);
-          if (k + e < len) A::d_add(s, rv[e], rv[e]);
+          if (k + e < len) A::d_add(s[e], rv[e], rv[e]);
         }
         A::stvv(r + off + k, rv);
+        if constexpr (LINE) {
+#pragma unroll
+          for (int e = 0; e < V; e++) xr[cc.seg * SEG + k + e] = rv[e];
+        }
       }
       __syncwarp();
       if (cc.seg == nseg - 1) {
-        A::d_merge(arr, s);
-        A::d_addw(arho, wrow, s);
-        s = A::d_init();
+#pragma unroll
+        for (int e = 1; e < V; e++) A::d_merge(s[0], s[e]);
+        A::d_merge(arr, s[0]);
+        if constexpr (LINE) {
+          // z = T^-1 r on the ring; rho += (mu / c) ||F r||^2; w = D z
+          typename A::dacc sz = A::d_init();
+          ring_solve<A>(xr, np, lmu, sz, lane);
+          A::d_addw(arho, wrow, sz);
+          const size_t ro = cc.off;
+          for (int k = lane * V; k < np; k += 32 * V) {
+            val wv_[V];
+#pragma unroll
+            for (int e = 0; e < V; e++) wv_[e] = A::mul(lgd, xr[k + e]);
+            A::stvv(wv + ro + k, wv_);
+          }
+          __syncwarp();
+        } else {
+          A::d_addw(arho, wrow, s[0]);
+        }
+#pragma unroll
+        for (int e = 0; e < V; e++) s[e] = A::d_init();
       }
       advance(cc);
     }
@@ -749,6 +892,16 @@ __global__ void __launch_bounds__(NT)
       __threadfence();
       const double rr = block_sum_array<NT>(P.part_b, P.tiles_b, 2, red);
       const double rho = block_sum_array<NT>(P.part_b + 1, P.tiles_b, 2, red);
+      if (setup) {
+        if (tid == 0) {
+          setup_out[0] = rr;
+          setup_out[1] = rho;
+          stt->ticket_b = 0u;
+          __threadfence();
+        }
+        __syncthreads();
+        continue;
+      }
       if (tid == 0) {
         const double relres = sqrt(rr) / sqrt(stt->bb);
         stt->relres = relres;

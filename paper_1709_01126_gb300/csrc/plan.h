@@ -25,6 +25,8 @@ struct ArithData {
   int2 *d_work_a = nullptr, *d_work_b = nullptr;
   int *d_nwork = nullptr; // [tiles_a, tiles_b]
   void *coef = nullptr; // scaled metric table [6][nr][ntp] in the arithmetic's type
+  void *lcoef = nullptr; // phi-line table [3][nr][ntp]: mu, mu / c, D mu / c
+  bool graph_line = false; // the captured graph launches the phi-line update
   ProbDev *d_prob = nullptr;
   SolveState *d_state = nullptr;
   double *part_a = nullptr, *part_b = nullptr;
@@ -75,6 +77,7 @@ struct Plan {
   int nsm = 0;
   std::vector<cudaEvent_t> ev;
   bool freeze_poll = false; // testing hook: the host re-reads a stale state snapshot
+  bool line = false;         // the solve in progress uses the phi-line preconditioner
   double *d_hist = nullptr;  // residual history of the last PCG run (opts.history)
   int hist_alloc = 0, hist_n = 0;
 };
@@ -85,6 +88,8 @@ bool is_device_ptr(const void *p);
 int plan_device_init(Plan *P);
 void plan_free(Plan *P);
 int ensure_arith(Plan *P, int ai);
+// phi-line table of arithmetic ai (AR_F64 or AR_F32), built on first use
+int ensure_line(Plan *P, int ai);
 size_t workspace_bytes(const Plan *P);
 int ensure_workspace(Plan *P);
 void *ws_vec(const Plan *P, int v, size_t es);

@@ -225,17 +225,54 @@ int ensure_arith(Plan *P, int ai) {
   return POT3D_OK;
 }
 
+// Phi-line table: per (i, j) ring, T = d - c (S + S^-1) with d = D_ij and
+// c = c^ph_ij factors as (c / mu)(1 - mu S)(1 - mu S^-1) with
+// mu + 1 / mu = d / c (the root below 1, in the form without cancellation);
+// the update kernel needs mu, mu / c (rho = (mu / c) ||F r||^2) and
+// D mu / c (w = D z).  Layout [3][nr][ntp] like the metric table.
+int ensure_line(Plan *P, int ai) {
+  ArithData &A = P->ar[ai];
+  if (A.lcoef) return POT3D_OK;
+  const int nr = P->nr, nt = P->nt, ntp = P->ntp;
+  const size_t R = P->R, RP = (size_t)nr * ntp;
+  std::vector<double> t(3 * RP, 0.0);
+  for (int i = 0; i < nr; i++)
+    for (int j = 0; j < nt; j++) {
+      const size_t row = (size_t)i * nt + j, o = (size_t)i * ntp + j;
+      const double d = P->c64h[C64_D * R + row], c = P->c64h[C64_PH * R + row];
+      const double mu = 2.0 * c / (d + std::sqrt((d - 2.0 * c) * (d + 2.0 * c)));
+      t[o] = mu;
+      t[RP + o] = mu / c;
+      t[2 * RP + o] = d * (mu / c);
+    }
+  int rc;
+  if (ai == AR_F64) {
+    rc = upload((double **)&A.lcoef, t);
+  } else {
+    std::vector<float> h(t.size());
+    for (size_t u = 0; u < t.size(); u++) h[u] = (float)t[u];
+    rc = upload((float **)&A.lcoef, h);
+  }
+  return rc;
+}
+
 // ----------------------------------------------------------- workspace
+// Vectors: x~, r, p~0, p~1, q and, with the phi-line preconditioner, w in
+// the iteration's arithmetic; x64, r64 in FP64 for refinement.
 size_t workspace_bytes(const Plan *P) {
   const size_t v8 = align256(P->npad * 8), v4 = align256(P->npad * 4);
-  const size_t f64 = 5 * v8;
-  const size_t mixed = 5 * v4 + 2 * v8;
+  const int nv = P->opts.precond == POT3D_PC_PHI_LINE ? 6 : 5;
+  const size_t f64 = nv * v8;
+  const size_t mixed = nv * v4 + 2 * v8;
   return P->prec == POT3D_PREC_MIXED ? mixed : std::max(f64, mixed);
 }
 
 int ensure_workspace(Plan *P) {
-  if (P->ws) return POT3D_OK;
   const size_t b = workspace_bytes(P);
+  if (P->ws && P->ws_bytes >= b) return POT3D_OK;
+  if (P->ws && !P->ws_owned) return POT3D_ERR_INVALID_ARG; // the caller's buffer is too small
+  if (P->ws) cudaFree(P->ws);
+  P->ws = nullptr;
   if (cudaMalloc(&P->ws, b) != cudaSuccess) {
     cudaGetLastError();
     return POT3D_ERR_OOM;
@@ -245,12 +282,15 @@ int ensure_workspace(Plan *P) {
   return POT3D_OK;
 }
 
-// Vector v (0..4: x~, r, p~0, p~1, q) of an arithmetic with element size es;
-// FP64 refinement vectors x64, r64 follow the five FP32 vectors.
+// Vector v (0..4: x~, r, p~0, p~1, q; 5: w) of an arithmetic with element
+// size es; FP64 refinement vectors x64, r64 follow the FP32 vectors.
 void *ws_vec(const Plan *P, int v, size_t es) { return P->ws + v * align256(P->npad * es); }
-double *ws_x64(const Plan *P) { return (double *)(P->ws + 5 * align256(P->npad * 4)); }
+static int n_iter_vecs(const Plan *P) { return P->opts.precond == POT3D_PC_PHI_LINE ? 6 : 5; }
+double *ws_x64(const Plan *P) {
+  return (double *)(P->ws + n_iter_vecs(P) * align256(P->npad * 4));
+}
 double *ws_r64(const Plan *P) {
-  return (double *)(P->ws + 5 * align256(P->npad * 4) + align256(P->npad * 8));
+  return (double *)(P->ws + n_iter_vecs(P) * align256(P->npad * 4) + align256(P->npad * 8));
 }
 
 int stage(Plan *P, size_t bytes) {
@@ -358,7 +398,8 @@ int pot3d_set_stream(pot3d_plan_t *plan, void *s) {
 int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *o) {
   if (!plan || !o) return fail(POT3D_ERR_INVALID_ARG);
   if (o->max_iters < 0 || o->chunk < 0 || o->inner_tol < 0 || !(o->inner_tol < 1.0) ||
-      o->max_outer < 0 || o->verify < 0 || o->verify > 1)
+      o->max_outer < 0 || o->verify < 0 || o->verify > 1 || o->precond < 0 || o->precond > 1 ||
+      o->history < 0 || o->history > 1)
     return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);
   P->opts = *o;

@@ -184,7 +184,25 @@ static void launch_matvec(Plan *P, int ai) {
 
 static void launch_update(Plan *P, int ai) {
   ArithData &D = P->ar[ai];
+  if (P->line) {
+    // the shared memory fits: checked by line_setup before the solve
+    update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, nullptr,
+                             P->stream);
+    return;
+  }
   update_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->stream);
+}
+
+// Phi-line start of a PCG run (solve or refinement step): the update kernel
+// in its setup mode on the current r (alpha = 0) writes w = D T^-1 r for the
+// first matvec and ||r||^2, r.T^-1 r to sums[0..1].
+static int line_setup(Plan *P, int ai, double *sums) {
+  ArithData &D = P->ar[ai];
+  if (update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, sums,
+                               P->stream) != 0)
+    return POT3D_ERR_UNSUPPORTED; // the rings do not fit in shared memory
+  P->stats.launches += 1;
+  return POT3D_OK;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -239,11 +257,13 @@ int encode_coef_map(CUtensorMap *m, const void *coef, int es, const Plan *P, int
 int encode_tma_set(TmaSet *T, const ProbDev &h, const void *coef, const MvVariant &v,
                    const Plan *P) {
   const int es = v.es;
-  int rc = encode3d(&T->r, h.r, es, P, v.bw, v.rh);
+  // the matvec forms p~ from r (PC1: D z = r) or from w = D z (phi lines)
+  void *rsrc = h.w ? h.w : h.r;
+  int rc = encode3d(&T->r, rsrc, es, P, v.bw, v.rh);
   if (!rc) rc = encode3d(&T->p0, h.p0, es, P, v.bw, v.rh);
   if (!rc) rc = encode3d(&T->p1, h.p1, es, P, v.bw, v.rh);
   if (!rc) rc = encode3d(&T->x, h.x, es, P, v.tk, v.tj);
-  if (!rc) rc = encode3d(&T->rw, h.r, es, P, v.al, v.rh);
+  if (!rc) rc = encode3d(&T->rw, rsrc, es, P, v.al, v.rh);
   if (!rc) rc = encode3d(&T->p0w, h.p0, es, P, v.al, v.rh);
   if (!rc) rc = encode3d(&T->p1w, h.p1, es, P, v.al, v.rh);
   if (!rc) rc = encode_coef_map(&T->cf, coef, es, P, v.tj);
@@ -299,7 +319,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
     // while chunk N+1 runs, so the GPU does not idle on the round trip.  A
     // chunk queued after the solve stopped does nothing (its kernels see the
     // status and exit).
-    if (graphs && (!D.graph || D.graph_chunk != chunk)) {
+    if (graphs && (!D.graph || D.graph_chunk != chunk || D.graph_line != P->line)) {
       if (D.graph) cudaGraphExecDestroy(D.graph);
       D.graph = nullptr;
       cudaGraph_t g;
@@ -313,6 +333,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
       cudaGraphDestroy(g);
       CTRY(e);
       D.graph_chunk = chunk;
+      D.graph_line = P->line;
     }
     SolveState *snap[2] = {P->h_state, P->h_state + 1};
     auto enqueue = [&](int b) -> int {
@@ -399,7 +420,8 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
 }
 
 template <class A>
-static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, void *q) {
+static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, void *q,
+                      void *w = nullptr) {
   ArithData &D = P->ar[ai];
   ProbDev &h = D.h_prob;
   h = ProbDev{};
@@ -425,6 +447,8 @@ static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, voi
   h.part_a = D.part_a;
   h.part_b = D.part_b;
   h.st = D.d_state;
+  h.w = w;
+  h.lcoef = w ? D.lcoef : nullptr;
 }
 
 static int status_code(int st) {
@@ -506,6 +530,11 @@ static int stage_io(Plan *P, const double *br, double *phi, double *B, bool phi_
 template <class A>
 static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi, int *iters) {
   TRY(ensure_arith(P, ai));
+  P->line = P->opts.precond == POT3D_PC_PHI_LINE;
+  if (P->line) {
+    if (!update_line_launcher(ai)) return fail(POT3D_ERR_UNSUPPORTED);
+    TRY(ensure_line(P, ai));
+  }
   TRY(ensure_workspace(P));
   const bool x0 = P->opts.use_x0 != 0;
   Io io;
@@ -513,15 +542,16 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   const size_t es = sizeof(typename A::st);
   void *x = ws_vec(P, 0, es), *r = ws_vec(P, 1, es), *p0 = ws_vec(P, 2, es),
        *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
+  void *w = P->line ? ws_vec(P, 5, es) : nullptr;
   ArithData &D = P->ar[ai];
-  fill_prob<A>(P, ai, x, r, p0, p1, q);
+  fill_prob<A>(P, ai, x, r, p0, p1, q, w);
   TRY(build_tma(P, ai));
   cudaStream_t s = P->stream;
   // the Br of the right-hand side (closed wall: balanced), kept for the field
   prepare_br(P, io.br, P->d_br_last, P->d_part, P->d_sums + 6, s);
   const double *brs = P->d_br_last;
   P->have_br = true;
-  CTRY(cudaMemsetAsync(P->ws, 0, 5 * ((P->npad * es + 255) & ~(size_t)255), s));
+  CTRY(cudaMemsetAsync(P->ws, 0, (P->line ? 6 : 5) * ((P->npad * es + 255) & ~(size_t)255), s));
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = aux_grid(P, n0);
   k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(brs, P->d_S, P->d_c64, P->nr, P->nt, P->np,
@@ -567,7 +597,13 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   }
   CTRY(cudaGetLastError());
   memset(&P->stats, 0, sizeof(P->stats));
-  P->stats.launches = x0 ? 7 : 4;
+  if (P->line) {
+    // w_0 = D T^-1 r_0 and rho_0 = r_0 . T^-1 r_0 (scaled units)
+    TRY(line_setup(P, ai, P->d_sums + 4));
+    k_set_rho<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4);
+    P->stats.launches += 1;
+  }
+  P->stats.launches += x0 ? 7 : 4;
   TRY(iterate<A>(P, ai));
   P->stats.launches += 1;
   k_finish<A><<<aux_grid(P, P->n), kAuxThreads, 0, s>>>(D.d_prob, P->d_c64, io.phi, 1);
@@ -602,6 +638,8 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
 static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *outer,
                        int *inner) {
   TRY(ensure_arith(P, AR_F32));
+  P->line = P->opts.precond == POT3D_PC_PHI_LINE;
+  if (P->line) TRY(ensure_line(P, AR_F32));
   TRY(ensure_workspace(P));
   const bool x0 = P->opts.use_x0 != 0;
   Io io;
@@ -610,8 +648,9 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   ArithData &D = P->ar[AR_F32];
   void *x = ws_vec(P, 0, 4), *r = ws_vec(P, 1, 4), *p0 = ws_vec(P, 2, 4), *p1 = ws_vec(P, 3, 4),
        *q = ws_vec(P, 4, 4);
+  void *w = P->line ? ws_vec(P, 5, 4) : nullptr;
   double *x64 = ws_x64(P), *r64 = ws_r64(P);
-  fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q);
+  fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q, w);
   TRY(build_tma(P, AR_F32));
   CTRY(cudaMemcpyAsync(D.d_prob, &D.h_prob, sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   // the Br of the right-hand side (closed wall: balanced), kept for the field
@@ -619,7 +658,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   const double *brs = P->d_br_last;
   P->have_br = true;
   const size_t v4 = (P->npad * 4 + 255) & ~(size_t)255;
-  CTRY(cudaMemsetAsync(P->ws, 0, 5 * v4, s));
+  CTRY(cudaMemsetAsync(P->ws, 0, (P->line ? 6 : 5) * v4, s));
   CTRY(cudaMemsetAsync(x64, 0, P->npad * 8, s));
   CTRY(cudaMemsetAsync(r64, 0, P->npad * 8, s));
   if (x0)
@@ -669,6 +708,8 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->ntp, P->np,
                                                         P->pitch, new_scale, (float *)r, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 4);
+    // phi lines: w = D T^-1 r32 and rho = r32 . T^-1 r32 replace the sums
+    if (P->line) TRY(line_setup(P, AR_F32, P->d_sums + 4));
     CTRY(cudaMemsetAsync(x, 0, v4, s));
     int iter0 = 0;
     if (resumable && !restart) {
@@ -811,7 +852,9 @@ int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double 
                                                             P->d_poles);
   FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd, P->closed ? 1 : 0};
   const size_t tot = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
-  const int gf = (int)std::min<size_t>(P->R, (size_t)8 * P->nsm);
+  if (P->n >= (1ull << 31)) return fail(POT3D_ERR_TOO_LARGE); // 32-bit cell index
+  const int gf = (int)std::min<size_t>((P->n + kFieldThreads - 1) / kFieldThreads,
+                                       (size_t)8 * P->nsm);
   k_field<<<gf, kFieldThreads, 0, s>>>(io.phi, d_br, P->d_poles, T, P->nr, P->nt, P->np, io.B);
   P->stats.launches = 2;
   CTRY(cudaGetLastError());
@@ -944,6 +987,7 @@ template <class A>
 int tune_arith(Plan *P, int ai, TuneVal *best) {
   TRY(ensure_arith(P, ai));
   TRY(ensure_workspace(P));
+  P->line = false; // the tuner times the diagonal-scaling kernels
   ArithData &D = P->ar[ai];
   const size_t es = sizeof(typename A::st);
   cudaStream_t s = P->stream;

@@ -26,15 +26,24 @@ struct MvVariant {
 const MvVariant *mv_variants(int ai, int *count);
 // The update kernel of arithmetic ai.
 KLaunch update_launcher(int ai);
+// The update kernel with the phi-line preconditioner (FP64 and FP32 only;
+// null for double-float): ring buffers of `pitch` values per warp, and the
+// setup mode when setup_out is non-null.  Returns 0, or -1 (nothing
+// launched) when the ring buffers do not fit in a block's shared memory.
+using KLineLaunch = int (*)(const ProbDev *, const int2 *, const int *, int grid, int pitch,
+                            double *setup_out, cudaStream_t);
+KLineLaunch update_line_launcher(int ai);
 // resident blocks per SM of arithmetic ai's update kernel (0: unknown)
 int update_occupancy(int ai);
 
 // Update kernel configurations per arithmetic: threads per block, bytes of
-// r (and of q) per warp stage, stages per warp.  The FP64 kernel is bound by
-// the FP64 unit; the HBM-bound ones keep more segments in flight.
+// r (and of q) per warp stage, stages per warp.  Two blocks of 8 warps per
+// SM with one segment in flight per warp beat one block with four in
+// flight (FP32 at 151 x 301 x 601 under ncu: 59.7 against 68.3 us): the
+// per-row work of the update is latency-bound and needs the warps.
 constexpr int kUpdSegBytes = 2560;
 constexpr int kUpdThreadsF64 = 256, kUpdStagesF64 = 2;
-constexpr int kUpdThreadsDF = 128, kUpdStagesDF = 4;
-constexpr int kUpdThreadsF32 = 128, kUpdStagesF32 = 5;
+constexpr int kUpdThreadsDF = 256, kUpdStagesDF = 2;
+constexpr int kUpdThreadsF32 = 256, kUpdStagesF32 = 2;
 
 } // namespace pot3d

@@ -35,6 +35,9 @@ POT3D_POLE_AVERAGE = 0
 
 PRECISIONS = {"fp64": POT3D_PREC_FP64, "df": POT3D_PREC_FP64_DF, "mixed": POT3D_PREC_MIXED}
 OUTER = {"source": POT3D_OUTER_SOURCE_SURFACE, "closed": POT3D_OUTER_CLOSED_WALL}
+POT3D_PC_JACOBI = 0
+POT3D_PC_PHI_LINE = 1
+PRECONDS = {"jacobi": POT3D_PC_JACOBI, "philine": POT3D_PC_PHI_LINE}
 
 
 class pot3d_grid_t(ctypes.Structure):
@@ -53,7 +56,7 @@ class pot3d_opts_t(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("mixed_restart", ctypes.c_int), ("verify", ctypes.c_int),
-                ("history", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("history", ctypes.c_int)]
 
 
 POT3D_FLAG_ABOVE_TOL = 1
@@ -271,10 +274,12 @@ class Plan:
             pass
 
     def set_opts(self, max_iters=0, use_x0=0, chunk=0, use_graphs=0, time_kernels=0,
-                 inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0, history=0):
+                 inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0, precond=0, history=0):
+        """pot3d_set_opts; precond: 0 / "jacobi" or 1 / "philine"."""
+        pc = PRECONDS.get(precond, precond)
         o = pot3d_opts_t(int(max_iters), int(use_x0), int(chunk), int(use_graphs), int(time_kernels),
                          float(inner_tol), int(max_outer), int(mixed_restart), int(verify),
-                         int(history))
+                         int(pc), int(history))
         _check(load().pot3d_set_opts(self.h, ctypes.byref(o)), "pot3d_set_opts")
 
     def set_stream(self, stream_handle):
@@ -377,7 +382,7 @@ class Batch:
     """Owns a pot3d_batch_t (continuous batching of mixed-precision solves)."""
 
     def __init__(self, max_bytes: int, max_slots: int = 256, inner_tol=0.0, max_outer=0,
-                 max_iters=0, mixed_restart=0):
+                 max_iters=0, mixed_restart=0, precond=0):
         L = load()
         h = L.pot3d_batch_create(int(max_bytes), int(max_slots))
         if not h:
@@ -385,8 +390,12 @@ class Batch:
         self.h = h
         self.max_slots = int(max_slots)
         o = pot3d_opts_t(int(max_iters), 0, 0, 0, 0, float(inner_tol), int(max_outer),
-                         int(mixed_restart), 0, 0)
-        _check(L.pot3d_batch_set_opts(h, ctypes.byref(o)), "pot3d_batch_set_opts")
+                         int(mixed_restart), 0, int(PRECONDS.get(precond, precond)), 0)
+        rc = L.pot3d_batch_set_opts(h, ctypes.byref(o))
+        if rc != POT3D_OK:
+            L.pot3d_batch_destroy(h)
+            self.h = None
+            raise Pot3dError(rc, "pot3d_batch_set_opts")
 
     def close(self):
         if getattr(self, "h", None):
