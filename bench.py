@@ -479,6 +479,8 @@ def run_gpu(args):
         variants[pv] = v
     if variants:
         result["variants"] = variants
+    if ws == 1 and args.precond_compare:
+        result["precond_comparison"] = precond_record(pot3d, torch, dev, br_d)
     if ws == 1 and args.serve_requests > 0:
         # the second half of the metric: mixed + batched serving vs FP64
         # one-at-a-time on one seeded stream (not part of the timed PCG steps)
@@ -489,6 +491,48 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     barrier(dist, dev)
     return 0
+
+
+def precond_record(pot3d, torch, dev, br_d, steps=2):
+    """Time to solution of the same 151x301x601 solve to 1e-10 with diagonal
+    scaling (PC1, the paper's) and with the phi-line preconditioner, in FP64
+    and in the mixed path: PCG iterations, seconds per solve (CUDA events on
+    torch's stream, after one warm-up solve) and the FP64 residual of the
+    result."""
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    phi = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
+    for prec in ("fp64", "mixed"):
+        out[prec] = {}
+        for pc in ("jacobi", "philine"):
+            plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=prec, precond=pc)
+            plan.autotune(4 if prec == "mixed" else 0)
+            plan.set_opts(precond=pc)
+
+            def solve():
+                if prec == "mixed":
+                    rc, o, it = plan.solve_mixed(br_d, TOL, phi)
+                else:
+                    rc, it = plan.solve(br_d, TOL, phi)
+                return it
+
+            solve()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = [solve() for _ in range(steps)]
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            sec = e0.elapsed_time(e1) / 1e3 / steps
+            st = plan.stats()
+            out[prec][pc] = {"iters": its[-1], "outer": st["outer_iters"], "s_per_solve": sec,
+                             "relres_fp64": st["relres_fp64"],
+                             "iters_per_s": its[-1] / sec}
+            plan.close()
+        j, l = out[prec]["jacobi"], out[prec]["philine"]
+        out[prec]["speedup_time_to_solution"] = j["s_per_solve"] / l["s_per_solve"]
+        out[prec]["iteration_ratio"] = j["iters"] / l["iters"]
+    return out
 
 
 def serve_record(requests, batch_k=16, inner_tol=0.0):
@@ -517,24 +561,33 @@ def serve_record(requests, batch_k=16, inner_tol=0.0):
     budget = int(min(0.5 * free, 96e9))
     batched = serve.run_batched(reqs, inputs, batch_bytes=budget, k=batch_k,
                                 inner_tol=inner_tol)
+    batched_l = serve.run_batched(reqs, inputs, batch_bytes=budget, k=batch_k,
+                                  inner_tol=inner_tol, precond="philine")
     base = serve.run_fp64_serial(reqs, inputs)
     # capacity: the same requests all present at t = 0
     sat_reqs = [serve.Request(r.rid, r.grid, 0.0, r.seed) for r in reqs]
     sat = serve.run_batched(sat_reqs, inputs, batch_bytes=budget, k=batch_k,
                             inner_tol=inner_tol).summary()
+    sat_l = serve.run_batched(sat_reqs, inputs, batch_bytes=budget, k=batch_k,
+                              inner_tol=inner_tol, precond="philine").summary()
     clocks = clk.stop()
-    b, f = batched.summary(), base.summary()
+    b, bl, f = batched.summary(), batched_l.summary(), base.summary()
     return {"requests": requests, "arrival_rate_per_s": rate,
             "workload": "serving stream of %d solves, Poisson arrivals at %.3f/s (1.5x FP64 "
                         "rate), grids %s, tol 1e-10" % (requests, rate, serve.GRIDS),
             "batch_arena_bytes": budget, "step_iters": batch_k,
-            "batched": b, "fp64_one_at_a_time": f,
+            "batched": b, "batched_phi_line": bl, "fp64_one_at_a_time": f,
             "speedup_solves_per_s": b["solves_per_s"] / f["solves_per_s"],
             "p99_ratio_fp64_over_batched": f["p99_latency_s"] / b["p99_latency_s"],
+            "p99_ratio_fp64_over_batched_phi_line": f["p99_latency_s"] / bl["p99_latency_s"],
             "capacity_solves_per_s": {"batched_all_at_t0": sat["solves_per_s"],
                                       "batched_all_at_t0_max_relres_fp64": sat["max_relres_fp64"],
+                                      "batched_phi_line_all_at_t0": sat_l["solves_per_s"],
+                                      "batched_phi_line_all_at_t0_max_relres_fp64":
+                                          sat_l["max_relres_fp64"],
                                       "fp64_one_at_a_time": rate64,
-                                      "ratio": sat["solves_per_s"] / rate64},
+                                      "ratio": sat["solves_per_s"] / rate64,
+                                      "ratio_phi_line": sat_l["solves_per_s"] / rate64},
             "fp64_calibration_s": dict(zip(["x".join(map(str, g)) for g in serve.GRIDS], times)),
             "clocks": clocks}
 
@@ -627,6 +680,11 @@ def run_profile_case(args):
     else:
         plan.solve(br_d, TOL, phi, check=False)
     torch.cuda.synchronize()
+    if args.profile_field:
+        B = torch.empty(sum(plan.field_sizes()), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            plan.field(phi, br_d, B)
+        torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "iters": plan.stats()["iters"]}))
     plan.close()
     return 0
@@ -694,6 +752,8 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
+    ap.add_argument("--profile-field", action="store_true",
+                    help="with --profile-case: also three field evaluations")
     ap.add_argument("--workload", default="pcg", choices=["pcg", "serve", "large", "large-solve"])
     ap.add_argument("--large-precs", default="df,mixed",
                     help="precisions of --workload large-solve, comma-separated")
@@ -703,6 +763,8 @@ def main():
                     help="large-solve: FP64/double-float restart on the FP64 residual (opts.verify)")
     ap.add_argument("--large-iters", type=int, default=200)
     ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--no-precond-compare", dest="precond_compare", action="store_false",
+                    help="skip the diagonal vs phi-line preconditioner comparison")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the serving record in the default run (0: none)")
     ap.add_argument("--batch-k", type=int, default=16)

@@ -83,8 +83,10 @@ struct Slot {
   double *phi = nullptr;
   double tol = 0.0;
   size_t off = 0, bytes = 0;
-  float *v32[5] = {}; // x~, r, p~0, p~1, q
+  float *v32[6] = {}; // x~, r, p~0, p~1, q; w (phi-line preconditioner)
   double *x64 = nullptr, *r64 = nullptr, *part_a = nullptr, *part_b = nullptr, *part_aux = nullptr;
+  int2 *own_work = nullptr; // phi lines: this solve's update items, for its setup launches
+  int *own_nwork = nullptr;
   int outer = 0, inner = 0, status = POT3D_OK, iter0 = 0;
   bool resumable = false; // the inner PCG stopped cleanly and may continue
   double relres = INFINITY, prev = INFINITY, scale = 1.0;
@@ -118,6 +120,8 @@ struct pot3d_batch {
   int work_cap = 0;
   unsigned var_mask = 0, graph_mask = 0; // variants with work now / in the graph
   int cap_of[8] = {};                    // grid of each list in the captured graph
+  bool line = false;                     // inner solves use the phi-line preconditioner
+  int ring_pitch = 0;                    // phi lines: ring buffers of the captured graph
   bool dirty = true;
   cudaStream_t stream = nullptr, own_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -138,13 +142,15 @@ int grid_for(const Batch *B, size_t n) {
 
 // Arena bytes of one solve: FP32 x~, r, p~0, p~1, q; FP64 x64, r64; the
 // partial slots of its matvec and update items and of its FP64 reductions.
-size_t slot_bytes(const Plan *P, int nsm) {
+size_t slot_bytes(const Plan *P, int nsm, bool line) {
   const ArithData &D = P->ar[AR_F32];
   const size_t v4 = al(P->npad * 4), v8 = al(P->npad * 8);
   // closed wall: a balanced copy of Br
   const size_t brb = P->closed ? al(sizeof(double) * P->nt * P->np) : 0;
+  // phi lines: w, and the solve's own update work list and its length
+  const size_t lin = line ? v4 + al(sizeof(int2) * D.tiles_b) + al(sizeof(int)) : 0;
   return 5 * v4 + 2 * v8 + al(sizeof(double) * D.tiles_a) + al(sizeof(double) * 2 * D.tiles_b) +
-         al(sizeof(double) * 2 * 4 * nsm) + brb;
+         al(sizeof(double) * 2 * 4 * nsm) + brb + lin;
 }
 
 // Rebuild and upload the concatenated work lists of the occupied slots:
@@ -195,6 +201,19 @@ int rebuild_work(Batch *B) {
   // the host vectors above are pageable and local: finish the copies here
   if (cudaStreamSynchronize(B->stream) != cudaSuccess) return POT3D_ERR_CUDA;
   B->var_mask = mask;
+  if (B->line) {
+    // ring buffers for the longest ring among the running solves
+    int rp = 0;
+    for (int s = 0; s < B->max_slots; s++) {
+      const Slot &S = B->slots[s];
+      if (S.phase != PH_FREE && S.phase != PH_DONE) rp = std::max(rp, S.plan->pitch);
+    }
+    if (rp > B->ring_pitch) {
+      B->ring_pitch = rp;
+      if (B->graph) cudaGraphExecDestroy(B->graph);
+      B->graph = nullptr;
+    }
+  }
   // a captured graph launches cap_of[v] blocks per list: grow (and
   // re-capture) when a list outgrows it, in steps to limit re-captures
   for (int v = 0; v < nl; v++) {
@@ -218,6 +237,12 @@ void launch_iteration(Batch *B) {
     if (!(B->graph_mask & (1u << v))) continue;
     vs[v].launch(B->d_probs, B->d_work + (size_t)v * B->work_cap, B->d_nwork + v,
                  std::max(1, B->cap_of[v]), B->stream);
+  }
+  if (B->line) {
+    update_line_launcher(AR_F32)(B->d_probs, B->d_work + (size_t)B->n_var * B->work_cap,
+                                 B->d_nwork + B->n_var, std::max(1, B->cap_of[B->n_var]),
+                                 B->ring_pitch, nullptr, B->stream);
+    return;
   }
   update_launcher(AR_F32)(B->d_probs, B->d_work + (size_t)B->n_var * B->work_cap,
                           B->d_nwork + B->n_var, std::max(1, B->cap_of[B->n_var]), B->stream);
@@ -243,6 +268,11 @@ void launch_inner_start(Batch *B, int s, double new_scale) {
   k_inner_rhs<kBThreads><<<g, kBThreads, 0, B->stream>>>(S.r64, dinv32, P->nr, P->nt, P->ntp, P->np,
                                                          P->pitch, new_scale, S.v32[1], S.part_aux);
   k_sum_pairs<kBThreads><<<1, kBThreads, 0, B->stream>>>(S.part_aux, g, B->d_isums + 2 * s);
+  if (B->line) {
+    // w = D T^-1 r32 and rho = r32 . T^-1 r32 of this solve replace its sums
+    update_line_launcher(AR_F32)(B->d_probs, S.own_work, S.own_nwork, P->ar[AR_F32].tiles_b,
+                                 P->pitch, B->d_isums + 2 * s, B->stream);
+  }
   const size_t v4 = al(P->npad * 4);
   const bool restart = B->opts.mixed_restart != 0;
   const double inner_tol = B->opts.inner_tol > 0 ? B->opts.inner_tol : default_inner_tol(P, restart);
@@ -418,8 +448,18 @@ int pot3d_batch_set_opts(pot3d_batch_t *batch, const pot3d_opts_t *o) {
   if (!batch || !o || o->inner_tol < 0 || !(o->inner_tol < 1.0) || o->max_outer < 0 ||
       o->max_iters < 0)
     return fail(POT3D_ERR_INVALID_ARG);
-  if (o->precond != POT3D_PC_JACOBI) return fail(POT3D_ERR_UNSUPPORTED); // diagonal scaling only
-  reinterpret_cast<Batch *>(batch)->opts = *o;
+  if (o->precond < 0 || o->precond > 1) return fail(POT3D_ERR_INVALID_ARG);
+  Batch *B = reinterpret_cast<Batch *>(batch);
+  const bool line = o->precond == POT3D_PC_PHI_LINE;
+  if (line != B->line) {
+    // the slot layout and the kernels depend on it: only an empty batch changes
+    for (const Slot &S : B->slots)
+      if (S.phase != PH_FREE) return fail(POT3D_ERR_BUSY);
+    B->line = line;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  B->opts = *o;
   return POT3D_OK;
 }
 
@@ -427,7 +467,7 @@ size_t pot3d_batch_bytes_needed(pot3d_batch_t *batch, const pot3d_plan_t *plan) 
   if (!batch || !plan) return 0;
   Plan *P = reinterpret_cast<Plan *>(const_cast<pot3d_plan_t *>(plan));
   if (ensure_arith(P, AR_F32)) return 0;
-  return slot_bytes(P, reinterpret_cast<Batch *>(batch)->nsm);
+  return slot_bytes(P, reinterpret_cast<Batch *>(batch)->nsm, reinterpret_cast<Batch *>(batch)->line);
 }
 
 int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *br, double tol,
@@ -445,9 +485,10 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
     }
   if (s < 0) return POT3D_ERR_BUSY;
   int rc = ensure_arith(P, AR_F32);
+  if (!rc && B->line) rc = ensure_line(P, AR_F32);
   if (rc) return fail(rc);
   const ArithData &D = P->ar[AR_F32];
-  const size_t bytes = slot_bytes(P, B->nsm);
+  const size_t bytes = slot_bytes(P, B->nsm, B->line);
   const size_t off = B->arena.alloc(bytes);
   if (off == SIZE_MAX) return POT3D_ERR_BUSY;
   Slot &S = B->slots[s];
@@ -478,6 +519,26 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
     double *brb = reinterpret_cast<double *>(p);
     prepare_br(P, br, brb, S.part_aux, B->d_isums + 2 * s, B->stream);
     S.br = brb;
+    p += al(sizeof(double) * P->nt * P->np);
+  }
+  if (B->line) {
+    S.v32[5] = reinterpret_cast<float *>(p);
+    p += v4;
+    S.own_work = reinterpret_cast<int2 *>(p);
+    p += al(sizeof(int2) * D.tiles_b);
+    S.own_nwork = reinterpret_cast<int *>(p);
+    std::vector<int2> ow(D.tiles_b);
+    for (int t = 0; t < D.tiles_b; t++) ow[t] = make_int2(s, t);
+    const int cnt = D.tiles_b;
+    // pageable sources: these copies complete before the calls return
+    if (cudaMemcpyAsync(S.own_work, ow.data(), sizeof(int2) * ow.size(), cudaMemcpyHostToDevice,
+                        B->stream) != cudaSuccess ||
+        cudaMemcpyAsync(S.own_nwork, &cnt, sizeof(int), cudaMemcpyHostToDevice, B->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(B->stream) != cudaSuccess) {
+      release_slot(B, s);
+      return fail(POT3D_ERR_CUDA);
+    }
   }
   // descriptor and TMA maps of the slot
   ProbDev &h = B->h_probs[s];
@@ -505,6 +566,8 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   h.part_b = S.part_b;
   h.st = B->d_states + s;
   h.tma = B->d_tmas + s;
+  h.w = B->line ? S.v32[5] : nullptr;
+  h.lcoef = B->line ? P->ar[AR_F32].lcoef : nullptr;
   TmaSet &T = B->h_tmas[s];
   int nv = 0;
   rc = encode_tma_set(&T, h, h.coef, mv_variants(AR_F32, &nv)[D.var], P);
@@ -521,6 +584,7 @@ int pot3d_batch_submit(pot3d_batch_t *batch, pot3d_plan_t *plan, const double *b
   // x64 = 0 and zeroed FP32 vectors (padding included); ||b||^2 for the
   // refinement test
   cudaMemsetAsync(B->arena_base + off, 0, 5 * v4 + 2 * v8, st);
+  if (B->line) cudaMemsetAsync(S.v32[5], 0, v4, st);
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = grid_for(B, n0);
   k_bstats<kBThreads><<<gb, kBThreads, 0, st>>>(S.br, P->d_S, P->d_c64, P->nr, P->nt, P->np,

@@ -256,6 +256,7 @@ class Plan:
             self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
             base = self._ws.data_ptr()
             aligned = (base + 255) // 256 * 256
+            self._ws_offset = aligned - base  # workspace starts here in self._ws
             _check(L.pot3d_set_workspace(h, aligned, nbytes), "pot3d_set_workspace")
 
     @property

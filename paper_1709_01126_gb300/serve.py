@@ -104,17 +104,19 @@ def prepare_inputs(requests):
 
 
 def run_batched(requests, inputs, batch_bytes: int, k: int = 16, max_slots: int = 256,
-                inner_tol: float = 0.0, verify: bool = True, keep: bool = False):
+                inner_tol: float = 0.0, verify: bool = True, keep: bool = False,
+                precond: str = "jacobi"):
     """Serves `requests` with the continuous-batching mixed-precision path.
     verify: recompute every served Phi's FP64 residual after the stream;
-    keep: keep the (Br, Phi) device tensors in the returned stats."""
+    keep: keep the (Br, Phi) device tensors in the returned stats;
+    precond: the inner solves' preconditioner ("jacobi" or "philine")."""
     import torch
 
     plans = {g: pot3d.Plan(*g, ratio=RATIO, precision="mixed") for g in {r.grid for r in requests}}
     for p in plans.values():
         p.autotune(4)  # FP32 kernels: tile variant, r-chunks, update rows
-    batch = pot3d.Batch(batch_bytes, max_slots=max_slots, inner_tol=inner_tol)
-    stats = ServeStats("mixed+batched")
+    batch = pot3d.Batch(batch_bytes, max_slots=max_slots, inner_tol=inner_tol, precond=precond)
+    stats = ServeStats("mixed+batched" + ("" if precond == "jacobi" else " (%s)" % precond))
     pending = sorted(requests, key=lambda r: r.arrival)
     waiting, live = [], {}
     t0 = time.perf_counter()

@@ -139,3 +139,36 @@ def test_c3_first_iterates(p3, oracle_mod):
         assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == 5
         assert rel(phi.cpu().numpy(), x5) <= bound
         plan.close()
+
+
+def test_c2_mixed_inner_dots_match_fp64_accumulation(p3, oracle_mod):
+    """The FP32 inner PCG forms its dot products from exact float products
+    summed in compensated float pairs per thread and row, then in FP64
+    across rows and blocks.  At 151 x 301 x 601, after 50 inner iterations,
+    sigma = sum D^-1 p~ q and ||r||^2 as the kernels summed them agree with
+    the same sums accumulated in FP64 from the FP32 vectors left in the
+    workspace, to 1e-12 relative."""
+    nr, nt, np_ = C2
+    br = syn.bipole_br(nt, np_, seed=1709)
+    plan = p3.Plan(*C2, ratio=1.02, precision="mixed", torch_workspace=True, max_iters=50,
+                   max_outer=1, use_graphs=-1)
+    phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
+    rc, outer, inner = plan.solve_mixed(torch.from_numpy(br).cuda(), 1e-10, phi, check=False)
+    assert inner == 50
+    st = plan.stats()
+    pitch = plan.info()["pitch"]
+    v4 = (nr * nt * pitch * 4 + 255) // 256 * 256
+    ws = plan._ws[plan._ws_offset:]
+
+    def vec(i):
+        return ws[i * v4: i * v4 + nr * nt * pitch * 4].view(torch.float32).reshape(
+            nr, nt, pitch)[:, :, :np_].cpu().numpy().astype(np.float64)
+
+    r, p_k, q = vec(1), vec(2 + (50 & 1)), vec(4)
+    g = oracle_mod.Grid(*C2, ratio=1.02)
+    dinv = (1.0 / g.diag()).astype(np.float32).astype(np.float64)
+    sigma_ref = np.sum(dinv * np.sum(p_k * q, axis=2))
+    rr_ref = np.sum(r * r)
+    assert abs(st["sigma"] - sigma_ref) <= 1e-12 * abs(sigma_ref), (st["sigma"], sigma_ref)
+    assert abs(st["rr"] - rr_ref) <= 1e-12 * rr_ref, (st["rr"], rr_ref)
+    plan.close()

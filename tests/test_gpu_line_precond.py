@@ -131,6 +131,3 @@ def test_phi_line_unsupported_paths(p3):
     rc, _ = plan.solve(br, 1e-10, phi, check=False)
     assert rc == p3.POT3D_ERR_UNSUPPORTED
     plan.close()
-    with pytest.raises(p3.Pot3dError) as ei:
-        p3.Batch(1 << 24, max_slots=2, precond="philine")
-    assert ei.value.code == p3.POT3D_ERR_UNSUPPORTED
