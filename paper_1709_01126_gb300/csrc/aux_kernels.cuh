@@ -371,8 +371,12 @@ __global__ void __launch_bounds__(NT)
 //   its [nt+1]: 1 / (theta-spacing across colatitude face f); f = 0 and nt
 //               use the mirror across the pole.
 //   irc [nr]  : 1 / r_i          isd [nt]: 1 / (sin th_j dphi)
+//   wt [nr*nt]: its[j] / r_i (colatitude faces j >= 1 of row (i, j))
+//   wp [nr*nt]: 1 / (r_i sin th_j dphi) (phi faces of row (i, j))
+//   wpole [2*nr]: 2 its[0] / r_i, 2 its[nt] / r_i (the two pole faces)
 struct FieldTabs {
   const double *irs, *its, *irc, *isd;
+  const double *wt, *wp, *wpole;
   int closed; // closed wall: Br = 0 on the outer face
 };
 
@@ -384,7 +388,10 @@ struct FieldTabs {
 // consecutive k, so every read of Phi (the cell, its lower radial and
 // northern neighbours, its phi successor) and every write is coalesced, and
 // Phi comes from HBM once (the neighbouring rows were read just before and
-// sit in L2).  Index arithmetic in 32 bits (the host checks n < 2^31).
+// sit in L2).  GB300's FP64 unit, not HBM, bounds this kernel: each face
+// costs one FP64 subtraction and one multiplication by a per-row factor
+// from the tables (6 FP64 operations per cell).  Index arithmetic in 32
+// bits (the host checks n < 2^31).
 constexpr int kFieldThreads = 256;
 static __global__ void __launch_bounds__(kFieldThreads)
     k_field(const double *__restrict__ phi, const double *__restrict__ br,
@@ -396,18 +403,20 @@ static __global__ void __launch_bounds__(kFieldThreads)
   for (unsigned e = blockIdx.x * kFieldThreads + threadIdx.x; e < n;
        e += gridDim.x * kFieldThreads) {
     const unsigned q = e / np, k = e - q * np, i = q / nt, j = q - i * nt;
-    const double v = phi[e], ir = T.irc[i];
+    const double v = phi[e];
     // ghost chosen so that dPhi/dr = Br on the inner face (Eq. 2)
-    B[e] = (i == 0) ? br[(size_t)j * np + k] : (v - phi[e - rplane]) * T.irs[i];
+    if (i == 0) B[e] = br[(size_t)j * np + k];
+    else B[e] = (v - phi[e - rplane]) * T.irs[i];
+    const size_t ot = ((size_t)i * (nt + 1) + j) * np + k;
     // ghost 2 avg - Phi across the north pole: the face value is the ring's
     // phi-average (Eq. 3)
-    const size_t ot = ((size_t)i * (nt + 1) + j) * np + k;
-    Bt[ot] = (j == 0) ? 2.0 * (v - poles[2 * i]) * T.its[0] * ir : (v - phi[e - np]) * T.its[j] * ir;
+    if (j == 0) Bt[ot] = (v - poles[2 * i]) * T.wpole[2 * i];
+    else Bt[ot] = (v - phi[e - np]) * T.wt[q];
     const unsigned ep = (k + 1 == (unsigned)np) ? e + 1 - np : e + 1;
-    Bp[e] = (phi[ep] - v) * ir * T.isd[j];
+    Bp[e] = (phi[ep] - v) * T.wp[q];
     // source surface: ghost -Phi (Phi = 0 there); closed wall: ghost Phi
     if (i == (unsigned)nr - 1) B[e + rplane] = T.closed ? 0.0 : (-2.0 * v) * T.irs[nr];
-    if (j == (unsigned)nt - 1) Bt[ot + np] = 2.0 * (poles[2 * i + 1] - v) * T.its[nt] * ir;
+    if (j == (unsigned)nt - 1) Bt[ot + np] = (poles[2 * i + 1] - v) * T.wpole[2 * i + 1];
   }
 }
 

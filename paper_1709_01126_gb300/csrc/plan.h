@@ -46,10 +46,11 @@ struct Plan {
   // host mesh (Sec. 2.2) and tables
   std::vector<double> rf, tf, rc, tc, drc, dtc;
   double dphi = 0.0;
-  std::vector<double> c64h, S, irs, its, irc, isd;
+  std::vector<double> c64h, S, irs, its, irc, isd, fwt, fwp, fwpole;
   // device constant tables
   double *d_c64 = nullptr, *d_S = nullptr, *d_irs = nullptr, *d_its = nullptr, *d_irc = nullptr,
-         *d_isd = nullptr, *d_poles = nullptr;
+         *d_isd = nullptr, *d_poles = nullptr, *d_fwt = nullptr, *d_fwp = nullptr,
+         *d_fwpole = nullptr;
   ArithData ar[3];
   // workspace (vectors)
   char *ws = nullptr;

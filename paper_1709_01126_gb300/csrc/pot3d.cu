@@ -150,6 +150,18 @@ static void build_tables(Plan *P) {
   for (int i = 0; i < nr; i++) P->irc[i] = 1.0 / P->rc[i];
   P->isd.resize(nt);
   for (int j = 0; j < nt; j++) P->isd[j] = 1.0 / (sc[j] * dphi);
+  // per-row factors of the field kernel (one multiplication per face)
+  P->fwt.assign(R, 0.0);
+  P->fwp.assign(R, 0.0);
+  P->fwpole.assign(2 * nr, 0.0);
+  for (int i = 0; i < nr; i++) {
+    for (int j = 0; j < nt; j++) {
+      P->fwt[(size_t)i * nt + j] = P->its[j] * P->irc[i];
+      P->fwp[(size_t)i * nt + j] = P->irc[i] * P->isd[j];
+    }
+    P->fwpole[2 * i] = 2.0 * P->its[0] * P->irc[i];
+    P->fwpole[2 * i + 1] = 2.0 * P->its[nt] * P->irc[i];
+  }
 }
 
 // Scaled, negated table of the iteration: Dinv, -c/D of the neighbour.

@@ -49,6 +49,9 @@ int plan_device_init(Plan *P) {
   CTRY(up(&P->d_its, P->its));
   CTRY(up(&P->d_irc, P->irc));
   CTRY(up(&P->d_isd, P->isd));
+  CTRY(up(&P->d_fwt, P->fwt));
+  CTRY(up(&P->d_fwp, P->fwp));
+  CTRY(up(&P->d_fwpole, P->fwpole));
   CTRY(cudaMalloc(&P->d_poles, sizeof(double) * 2 * P->nr));
   CTRY(cudaMalloc(&P->d_br_last, sizeof(double) * P->nt * P->np));
   if (P->closed) CTRY(cudaMalloc(&P->d_br_tmp, sizeof(double) * P->nt * P->np));
@@ -85,6 +88,9 @@ void plan_free(Plan *P) {
   cudaFree(P->d_its);
   cudaFree(P->d_irc);
   cudaFree(P->d_isd);
+  cudaFree(P->d_fwt);
+  cudaFree(P->d_fwp);
+  cudaFree(P->d_fwpole);
   cudaFree(P->d_poles);
   cudaFree(P->d_br_last);
   cudaFree(P->d_br_tmp);
@@ -850,7 +856,8 @@ int pot3d_field(pot3d_plan_t *plan, const double *phi, const double *br, double 
   }
   k_pole_avg<kAuxThreads><<<2 * P->nr, kAuxThreads, 0, s>>>(io.phi, P->nr, P->nt, P->np,
                                                             P->d_poles);
-  FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd, P->closed ? 1 : 0};
+  FieldTabs T{P->d_irs, P->d_its, P->d_irc, P->d_isd, P->d_fwt, P->d_fwp, P->d_fwpole,
+              P->closed ? 1 : 0};
   const size_t tot = (size_t)(P->nr + 1) * P->nt * P->np + (size_t)P->nr * (P->nt + 1) * P->np + P->n;
   if (P->n >= (1ull << 31)) return fail(POT3D_ERR_TOO_LARGE); // 32-bit cell index
   const int gf = (int)std::min<size_t>((P->n + kFieldThreads - 1) / kFieldThreads,

@@ -1,12 +1,24 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
-times (per-kernel event timing on, no graphs).
+times.
 
-- 151 x 301 x 601 (the benchmark workload): the first PCG iterates against
-  the oracle's; the full solve to 1e-10 against the stored oracle solve
-  (iteration count +-1, sampled Phi) and its true residual recomputed by the
-  oracle's operator.
+- 151 x 301 x 601 (the benchmark workload):
+  * the first 200 PCG iterates against the oracle's;
+  * full solves to 1e-10 and to 1e-12 against the stored oracle solves
+    (tests/golden/oracle_151x301x601.json, written by make_golden_large.py
+    from the oracle alone): Phi on a stratified sample of cells (every
+    boundary-folded layer: inner and source-surface layers, both pole rings,
+    the phi-wrap columns), the stopping iteration, the whole residual
+    history, and the true residual recomputed by the oracle's operator;
 - 401 x 801 x 1601 (514 M unknowns, the largest single-GPU case): the first
-  iterates against the oracle's.
+  200 iterates against the oracle's.
+
+Rounding-order bars.  Two correct FP64 PCG runs that add their dot products
+in different orders drift apart: the oracle itself, run with two OpenMP
+thread counts, gives iterates 200 that differ by about 2e-11 (relative L2)
+here, residual histories that differ by up to the stored
+max_rel_history_diff, and stopping iterations that differ by the stored
+spread.  Each bar below is a small multiple of the oracle's own spread,
+measured (live, or stored with the golden solve), never a fixed allowance.
 """
 import json
 import os
@@ -23,6 +35,8 @@ torch = pytest.importorskip("torch")
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                     "oracle_151x301x601.json")
 C2 = (151, 301, 601)
+# double-float's unit roundoff (2^-48) is 32 times FP64's
+ARITH_FACTOR = {"fp64": 1.0, "df": 32.0}
 
 
 @pytest.fixture(scope="module")
@@ -43,53 +57,103 @@ def c2(oracle_mod):
     return g, br, g.rhs(br)
 
 
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
 def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("prec,bound", [("fp64", 1e-10), ("df", 1e-9)])
-def test_c2_first_iterates(p3, oracle_mod, c2, prec, bound):
+def oracle_iterates(oracle_mod, g, b, k):
+    """The oracle's k-th iterate with all host threads, and its relative
+    distance to the same iterate under another reduction order (one thread
+    fewer): the oracle's own rounding spread."""
+    n = os.cpu_count() or 1
+    oracle_mod.set_threads(n)
+    x, _, _ = g.pcg(b, 1e-300, maxit=k)
+    oracle_mod.set_threads(max(1, n - 1) if n > 1 else 2)
+    y, _, _ = g.pcg(b, 1e-300, maxit=k)
+    oracle_mod.set_threads(n)
+    return x, rel(y, x)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_c2_first_200_iterates(p3, oracle_mod, c2, prec):
     g, br, b = c2
-    x20, it, st = g.pcg(b, 1e-300, maxit=20)
-    plan = p3.Plan(*C2, ratio=1.02, precision=prec, max_iters=20, time_kernels=1)
+    x, spread = oracle_iterates(oracle_mod, g, b, 200)
+    plan = p3.Plan(*C2, ratio=1.02, precision=prec, max_iters=200)
+    plan.autotune(0)  # the benchmark's kernel configuration
     phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
     rc, it_gpu = plan.solve(torch.from_numpy(br).cuda(), 1e-300, phi, check=False)
-    assert rc == p3.POT3D_ERR_NOT_CONVERGED and it_gpu == 20
-    assert rel(phi.cpu().numpy(), x20) <= bound
+    assert rc == p3.POT3D_ERR_NOT_CONVERGED and it_gpu == 200
+    d = rel(phi.cpu().numpy(), x)
+    assert d <= 4.0 * ARITH_FACTOR[prec] * max(spread, 1e-14), (d, spread)
     plan.close()
 
 
+def stop_band(gold, tol):
+    """Stopping iterations of the oracle under its stored reduction orders."""
+    key = "%g" % tol
+    stops = [gold["tol_" + key]["iters"]]
+    stops += [v["stop_" + key] for v in gold["other_thread_counts"].values()]
+    return min(stops), max(stops)
+
+
+@pytest.mark.parametrize("tol", [1e-10, 1e-12])
 @pytest.mark.parametrize("prec", ["fp64", "df", "mixed"])
-def test_c2_full_solve(p3, oracle_mod, c2, prec):
+def test_c2_full_solve(p3, oracle_mod, c2, gold, prec, tol):
     g, br, b = c2
-    with open(GOLD) as f:
-        gold = json.load(f)["tol_1e-10"]
-    plan = p3.Plan(*C2, ratio=1.02, precision=prec, time_kernels=1)
+    ref = gold["tol_%g" % tol]
+    idx = gold["sample_index"]
+    plan = p3.Plan(*C2, ratio=1.02, precision=prec, history=1)
+    plan.autotune(4 if prec == "mixed" else 0)
     phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
-    rc, it = plan.solve(torch.from_numpy(br).cuda(), 1e-10, phi)
+    rc, it = plan.solve(torch.from_numpy(br).cuda(), tol, phi)
+    st = plan.stats()
     x = phi.cpu().numpy()
     true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
-    xs = x.ravel()[gold["sample_index"]]
-    ref = np.array(gold["sample_phi"])
+    xs = x.ravel()[idx]
+    rs = np.array(ref["sample_phi"])
+    err = np.linalg.norm(xs - rs) / np.linalg.norm(rs)
+    # the library's own FP64 residual agrees with the oracle's recomputation
+    assert abs(st["relres_fp64"] - true_rel) <= 0.02 * true_rel
     if prec == "mixed":
         # refinement stops on the FP64 residual itself
-        assert true_rel <= 1.0001e-10
-        assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-6
-    else:
-        assert iteration_matches(it, gold, 1e-10), (it, gold["iters"])
-        assert true_rel <= (1.05e-10 if prec == "fp64" else 1.5e-10), true_rel
-        assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-9
+        assert true_rel <= tol * 1.0001, true_rel
+        assert err <= (1e-6 if tol >= 1e-10 else 1e-8), err
+        plan.close()
+        return
+    # Phi on the stratified sample (north_star bar: 1e-9)
+    assert err <= 1e-9, err
+    # the stopping iteration: +-1 of the oracle's, or inside the spread of
+    # the oracle's own stops under other reduction orders, +-1
+    lo, hi = stop_band(gold, tol)
+    assert abs(it - ref["iters"]) <= 1 or lo - 1 <= it <= hi + 1, (it, ref["iters"], lo, hi)
+    # the residual history follows the oracle's, within a small multiple of
+    # the oracle's own history spread
+    h = plan.history()
+    ho = np.array(gold["relres_history"]["values"])
+    m = min(len(h), len(ho))
+    spread = max(v["max_rel_history_diff"] for v in gold["other_thread_counts"].values())
+    dev = np.max(np.abs(h[:m] - ho[:m]) / ho[:m])
+    assert dev <= 4.0 * ARITH_FACTOR[prec] * spread, (dev, spread)
+    # the true residual: the recurrence's convergence claim up to the
+    # arithmetic's gap between recurrence and true residual (double-float
+    # carries five fewer bits, so its recurrence drifts further)
+    assert true_rel <= (tol * 1.05 if prec == "fp64" else tol * 1.5 + 3e-11), true_rel
     plan.close()
 
 
-def test_c2_df_verify_restarts_to_true_residual(p3, oracle_mod, c2):
+def test_c2_df_verify_restarts_to_true_residual(p3, oracle_mod, c2, gold):
     """Double-float PCG stopped by its recurrence residual at 1e-10 leaves a
     true residual slightly above 1e-10 here; with opts.verify it restarts
     from Phi with the FP64 residual and returns a true residual within tol
     (recomputed by the oracle)."""
     g, br, b = c2
-    with open(GOLD) as f:
-        gold = json.load(f)["tol_1e-10"]
+    ref = gold["tol_1e-10"]
     plan = p3.Plan(*C2, ratio=1.02, precision="df", verify=1)
     phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
     rc, it = plan.solve(torch.from_numpy(br).cuda(), 1e-10, phi)
@@ -98,47 +162,11 @@ def test_c2_df_verify_restarts_to_true_residual(p3, oracle_mod, c2):
     true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
     assert rc == 0 and true_rel <= 1.001e-10, (true_rel, st)
     assert abs(st["relres"] - true_rel) <= 1e-13
-    assert st["outer_iters"] >= 1 and it > gold["iters"]
+    assert st["outer_iters"] >= 1 and it > ref["iters"]
     xs = x.ravel()[gold["sample_index"]]
-    ref = np.array(gold["sample_phi"])
-    assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-9
+    rs = np.array(ref["sample_phi"])
+    assert np.linalg.norm(xs - rs) / np.linalg.norm(rs) <= 1e-9
     plan.close()
-
-
-def iteration_matches(it, gold, tol, band=0.05):
-    """The GPU stops at iteration `it`.  Near the end of this solve the
-    residual falls only about 0.4% per iteration, so rounding-order
-    differences over ~6000 CG steps shift the crossing of `tol` by a few
-    iterations.  Accept `it` when the oracle's own residual history puts
-    the crossing there within a `band` relative margin of `tol` (the
-    oracle's residual at it-1 is not far below tol and at it is not far
-    above); without a stored history, within 3 iterations."""
-    if "relres_tail" not in gold:
-        return abs(it - gold["iters"]) <= 3
-    t0, tail = gold["relres_tail_start"], gold["relres_tail"]
-    if not (t0 + 1 <= it < t0 + len(tail)):
-        return abs(it - gold["iters"]) <= 3
-    before, at = tail[it - 1 - t0], tail[it - t0]
-    return before >= tol * (1 - band) and at <= tol * (1 + band)
-
-
-def test_c3_first_iterates(p3, oracle_mod):
-    shape = (401, 801, 1601)
-    free, total = torch.cuda.mem_get_info()
-    if free < 30e9:
-        pytest.skip("needs about 25 GB of free device memory")
-    br = syn.bipole_br(shape[1], shape[2], seed=1709)
-    oracle_mod.set_threads(os.cpu_count() or 1)
-    g = oracle_mod.Grid(*shape, ratio=1.02)
-    x5, _, _ = g.pcg(g.rhs(br), 1e-300, maxit=5)
-    brd = torch.from_numpy(br).cuda()
-    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
-    for prec, bound in (("df", 1e-9), ("fp64", 1e-10)):
-        plan = p3.Plan(*shape, ratio=1.02, precision=prec, max_iters=5, time_kernels=1)
-        rc, it = plan.solve(brd, 1e-300, phi, check=False)
-        assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == 5
-        assert rel(phi.cpu().numpy(), x5) <= bound
-        plan.close()
 
 
 def test_c2_mixed_inner_dots_match_fp64_accumulation(p3, oracle_mod):
@@ -150,8 +178,9 @@ def test_c2_mixed_inner_dots_match_fp64_accumulation(p3, oracle_mod):
     workspace, to 1e-12 relative."""
     nr, nt, np_ = C2
     br = syn.bipole_br(nt, np_, seed=1709)
+    # the inner solve runs 50 iterations (no refinement hand-over before)
     plan = p3.Plan(*C2, ratio=1.02, precision="mixed", torch_workspace=True, max_iters=50,
-                   max_outer=1, use_graphs=-1)
+                   max_outer=1, use_graphs=-1, inner_tol=1e-20)
     phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
     rc, outer, inner = plan.solve_mixed(torch.from_numpy(br).cuda(), 1e-10, phi, check=False)
     assert inner == 50
@@ -172,3 +201,22 @@ def test_c2_mixed_inner_dots_match_fp64_accumulation(p3, oracle_mod):
     assert abs(st["sigma"] - sigma_ref) <= 1e-12 * abs(sigma_ref), (st["sigma"], sigma_ref)
     assert abs(st["rr"] - rr_ref) <= 1e-12 * rr_ref, (st["rr"], rr_ref)
     plan.close()
+
+
+def test_c3_first_200_iterates(p3, oracle_mod):
+    shape = (401, 801, 1601)
+    free, total = torch.cuda.mem_get_info()
+    if free < 30e9:
+        pytest.skip("needs about 25 GB of free device memory")
+    br = syn.bipole_br(shape[1], shape[2], seed=1709)
+    g = oracle_mod.Grid(*shape, ratio=1.02)
+    x, spread = oracle_iterates(oracle_mod, g, g.rhs(br), 200)
+    brd = torch.from_numpy(br).cuda()
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "df"):
+        plan = p3.Plan(*shape, ratio=1.02, precision=prec, max_iters=200)
+        rc, it = plan.solve(brd, 1e-300, phi, check=False)
+        assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == 200
+        d = rel(phi.cpu().numpy(), x)
+        assert d <= 4.0 * ARITH_FACTOR[prec] * max(spread, 1e-14), (prec, d, spread)
+        plan.close()
