@@ -671,11 +671,12 @@ def run_profile_case(args):
     pot3d.load()
     br_d = torch.from_numpy(make_br()).cuda()
     plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=args.profile_case,
-                      max_iters=args.profile_iters, use_graphs=-1)
+                      max_iters=args.profile_iters, use_graphs=-1, precond=args.precond)
     plan.autotune(4 if args.profile_case == "mixed" else 0)  # the bench's kernel configuration
     phi = torch.zeros(SHAPE, dtype=torch.float64, device="cuda")
     if args.profile_case == "mixed":
-        plan.set_opts(max_iters=args.profile_iters, use_graphs=-1, max_outer=1)
+        plan.set_opts(max_iters=args.profile_iters, use_graphs=-1, max_outer=1,
+                      precond=args.precond)
         plan.solve_mixed(br_d, TOL, phi, check=False)
     else:
         plan.solve(br_d, TOL, phi, check=False)
@@ -752,6 +753,8 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine"],
+                    help="with --profile-case: the preconditioner")
     ap.add_argument("--profile-field", action="store_true",
                     help="with --profile-case: also three field evaluations")
     ap.add_argument("--workload", default="pcg", choices=["pcg", "serve", "large", "large-solve"])
