@@ -86,7 +86,8 @@ struct ProbDev {
   int hist_cap;
   int pad2_;
   void *w;            // phi-line preconditioner: w = D M^-1 r (null: PC1)
-  const void *lcoef;  // phi-line table [3][nr][ntp]: mu, mu / c, D mu / c
+  const void *lcoef;  // phi-line table [6][nr][ntp]: mu, mu / c, D mu / c, mu^m,
+                      // mu^(np mod m), 1 / (1 - mu^np)  (m = ceil(np / 32))
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -599,30 +600,22 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // and F is a first-order recurrence around the ring, u_k = x_k + mu u_{k-1}
 // (indices mod n), whose periodic solution is exact: with u_{-1} the value
 // that closes the ring, u_{n-1} = mu^n u_{-1} + (the value reached from 0)
-// fixes u_{-1}.  F^T is the same recurrence run backwards.  A warp solves a
+// fixes u_{-1} = (that value) / (1 - mu^n).  F^T is the same recurrence run backwards.  A warp solves a
 // ring held in shared memory: every lane runs its contiguous chunk from a
 // zero carry, the chunk maps c -> mu^len c + s are composed across lanes by
 // a shuffle scan, the ring closure gives the carry into every chunk, and a
 // second pass applies the recurrence from the right carry.  Returns (in
 // acc) this lane's share of ||F x||^2; x is overwritten by F^T F x.
-template <class A>
-__device__ __forceinline__ typename A::val lane_pow(typename A::val mu, int e) {
-  typename A::val r = A::one(), b = mu;
-  while (e > 0) {
-    if (e & 1) r = A::mul(r, b);
-    b = A::mul(b, b);
-    e >>= 1;
-  }
-  return r;
-}
-
+// mu_m = mu^m and mu_rem = mu^(n mod m) for the lanes' chunk lengths
+// m = ceil(n / 32) and n mod m; inv = 1 / (1 - mu^n) closes the ring.
 template <class A>
 __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A::val mu,
-                                           typename A::dacc &acc, int lane) {
+                                           typename A::val mu_m, typename A::val mu_rem,
+                                           typename A::val inv, typename A::dacc &acc, int lane) {
   using val = typename A::val;
   const int m = (n + 31) >> 5;
   const int a = min(lane * m, n), b = min(a + m, n);
-  const val pm = lane_pow<A>(mu, b - a);
+  const val pm = (b - a == m) ? mu_m : (b == a ? A::one() : mu_rem);
   // ---- forward recurrence u_k = x_k + mu u_{k-1}
   val t = A::zero();
   for (int k = a; k < b; k++) t = A::fma(mu, t, x[k]);
@@ -640,8 +633,8 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
     Sx = A::zero();
     Px = A::one();
   }
-  val total = A::shfl_idx(S, 31), mun = A::shfl_idx(M, 31);
-  t = A::fma(Px, A::div(total, A::sub(A::one(), mun)), Sx); // carry into this chunk
+  val total = A::shfl_idx(S, 31);
+  t = A::fma(Px, A::mul(total, inv), Sx); // carry into this chunk
   for (int k = a; k < b; k++) {
     t = A::fma(mu, t, x[k]);
     x[k] = t;
@@ -668,8 +661,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
     Px = A::one();
   }
   total = A::shfl_idx(S, 0);
-  mun = A::shfl_idx(M, 0);
-  t = A::fma(Px, A::div(total, A::sub(A::one(), mun)), Sx);
+  t = A::fma(Px, A::mul(total, inv), Sx);
   for (int k = b - 1; k >= a; k--) {
     t = A::fma(mu, t, x[k]);
     x[k] = t;
@@ -745,7 +737,7 @@ __global__ void __launch_bounds__(NT)
     st *__restrict__ r = static_cast<st *>(P.r);
     const st *__restrict__ q = static_cast<const st *>(P.q);
     const coef *__restrict__ cf = static_cast<const coef *>(P.coef);
-    // phi-line table slabs: mu, mu / c, D mu / c
+    // phi-line table slabs: mu, mu / c, D mu / c, mu^m, mu^(np mod m), 1 / (1 - mu^np)
     const coef *__restrict__ lc = static_cast<const coef *>(P.lcoef);
     st *__restrict__ wv = static_cast<st *>(P.w);
     val *xr = ring + (size_t)wy * pitch;
@@ -802,7 +794,7 @@ __global__ void __launch_bounds__(NT)
     int issued = 0;
     for (; issued < min(units, STG - 1); issued++) issue(issued);
     int u = 0;
-    coef wrow{}, lmu{}, lgd{};
+    coef wrow{}, lmu{}, lgd{}, lmm{}, lmr{}, linv{};
     for (; u < units; u++) {
       if (issued < units) issue(issued++);
       if (cc.seg == 0) { // ahead of the wait
@@ -811,6 +803,9 @@ __global__ void __launch_bounds__(NT)
           lmu = lc[rj];
           wrow = lc[RT + rj];
           lgd = lc[2 * RT + rj];
+          lmm = lc[3 * RT + rj];
+          lmr = lc[4 * RT + rj];
+          linv = lc[5 * RT + rj];
         } else {
           wrow = cf[rj];
         }
@@ -850,7 +845,7 @@ __global__ void __launch_bounds__(NT)
         if constexpr (LINE) {
           // z = T^-1 r on the ring; rho += (mu / c) ||F r||^2; w = D z
           typename A::dacc sz = A::d_init();
-          ring_solve<A>(xr, np, lmu, sz, lane);
+          ring_solve<A>(xr, np, lmu, lmm, lmr, linv, sz, lane);
           A::d_addw(arho, wrow, sz);
           const size_t ro = cc.off;
           for (int k = lane * V; k < np; k += 32 * V) {

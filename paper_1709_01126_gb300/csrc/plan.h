@@ -25,7 +25,7 @@ struct ArithData {
   int2 *d_work_a = nullptr, *d_work_b = nullptr;
   int *d_nwork = nullptr; // [tiles_a, tiles_b]
   void *coef = nullptr; // scaled metric table [6][nr][ntp] in the arithmetic's type
-  void *lcoef = nullptr; // phi-line table [3][nr][ntp]: mu, mu / c, D mu / c
+  void *lcoef = nullptr; // phi-line table [6][nr][ntp] (see ensure_line)
   bool graph_line = false; // the captured graph launches the phi-line update
   ProbDev *d_prob = nullptr;
   SolveState *d_state = nullptr;

@@ -240,14 +240,17 @@ int ensure_arith(Plan *P, int ai) {
 // Phi-line table: per (i, j) ring, T = d - c (S + S^-1) with d = D_ij and
 // c = c^ph_ij factors as (c / mu)(1 - mu S)(1 - mu S^-1) with
 // mu + 1 / mu = d / c (the root below 1, in the form without cancellation);
-// the update kernel needs mu, mu / c (rho = (mu / c) ||F r||^2) and
-// D mu / c (w = D z).  Layout [3][nr][ntp] like the metric table.
+// the update kernel needs mu, mu / c (rho = (mu / c) ||F r||^2),
+// D mu / c (w = D z), and for the ring solve the powers mu^m and
+// mu^(np mod m) of the lanes' chunk lengths (m = ceil(np / 32)) and
+// 1 / (1 - mu^np).  Layout [6][nr][ntp] like the metric table.
 int ensure_line(Plan *P, int ai) {
   ArithData &A = P->ar[ai];
   if (A.lcoef) return POT3D_OK;
-  const int nr = P->nr, nt = P->nt, ntp = P->ntp;
+  const int nr = P->nr, nt = P->nt, ntp = P->ntp, np = P->np;
+  const int m = (np + 31) / 32, rem = np % m;
   const size_t R = P->R, RP = (size_t)nr * ntp;
-  std::vector<double> t(3 * RP, 0.0);
+  std::vector<double> t(6 * RP, 0.0);
   for (int i = 0; i < nr; i++)
     for (int j = 0; j < nt; j++) {
       const size_t row = (size_t)i * nt + j, o = (size_t)i * ntp + j;
@@ -256,6 +259,9 @@ int ensure_line(Plan *P, int ai) {
       t[o] = mu;
       t[RP + o] = mu / c;
       t[2 * RP + o] = d * (mu / c);
+      t[3 * RP + o] = std::pow(mu, m);
+      t[4 * RP + o] = std::pow(mu, rem);
+      t[5 * RP + o] = 1.0 / (1.0 - std::pow(mu, np));
     }
   int rc;
   if (ai == AR_F64) {
