@@ -145,7 +145,7 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-# captures summarised in profiles/k_matvec_k_update_151x301x601.md (same
+# captures summarised in profiles/k_matvec_151x301x601.md (same
 # kernels and tuned configuration as timed here)
 TRAFFIC = {"fp64": 1.2927e9, "df": 1.2851e9, "mixed": 0.6223e9}
 

@@ -618,6 +618,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
   const val pm = (b - a == m) ? mu_m : (b == a ? A::one() : mu_rem);
   // ---- forward recurrence u_k = x_k + mu u_{k-1}
   val t = A::zero();
+#pragma unroll 4
   for (int k = a; k < b; k++) t = A::fma(mu, t, x[k]);
   val M = pm, S = t;
 #pragma unroll
@@ -635,6 +636,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
   }
   val total = A::shfl_idx(S, 31);
   t = A::fma(Px, A::mul(total, inv), Sx); // carry into this chunk
+#pragma unroll 4
   for (int k = a; k < b; k++) {
     t = A::fma(mu, t, x[k]);
     x[k] = t;
@@ -643,6 +645,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
   __syncwarp();
   // ---- backward recurrence v_k = u_k + mu v_{k+1}
   t = A::zero();
+#pragma unroll 4
   for (int k = b - 1; k >= a; k--) t = A::fma(mu, t, x[k]);
   M = pm;
   S = t;
@@ -662,6 +665,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
   }
   total = A::shfl_idx(S, 0);
   t = A::fma(Px, A::mul(total, inv), Sx);
+#pragma unroll 4
   for (int k = b - 1; k >= a; k--) {
     t = A::fma(mu, t, x[k]);
     x[k] = t;
