@@ -708,7 +708,8 @@ def run_large_solve(args):
     out = {}
     for prec in [p for p in args.large_precs.split(",") if p]:
         plan = pot3d.Plan(*shape, ratio=args.large_ratio, precision=prec,
-                          max_iters=args.large_maxit, verify=1 if args.large_verify else 0)
+                          max_iters=args.large_maxit, verify=1 if args.large_verify else 0,
+                          precond=args.precond)
         tuned = plan.autotune(4 if prec == "mixed" else 0)
         phi.zero_()
         torch.cuda.synchronize()
@@ -723,6 +724,7 @@ def run_large_solve(args):
         if prec != "mixed":
             outer = plan.stats()["outer_iters"]  # residual replacements (verify)
         out[prec] = {"status": rc, "seconds": dt, "iters": it, "outer": outer,
+                     "precond": args.precond,
                      "verify": bool(args.large_verify) and prec != "mixed",
                      "iters_per_s": it / dt, "relres_fp64": plan.residual(br_d, phi),
                      "autotune": {"matvec_variant": tuned[0], "r_chunks": tuned[1]}}
@@ -754,7 +756,7 @@ def main():
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine"],
-                    help="with --profile-case: the preconditioner")
+                    help="the preconditioner of --profile-case and --workload large-solve")
     ap.add_argument("--profile-field", action="store_true",
                     help="with --profile-case: also three field evaluations")
     ap.add_argument("--workload", default="pcg", choices=["pcg", "serve", "large", "large-solve"])
