@@ -150,6 +150,7 @@ struct PF64 {
   static __device__ __forceinline__ val from_double(double x) { return x; }
   static __device__ __forceinline__ double to_double(val v) { return v; }
   // scalar helpers of the phi-line ring solve
+  static __device__ __forceinline__ dacc d_of(val v) { return {v}; }
   static __device__ __forceinline__ val one() { return 1.0; }
   static __device__ __forceinline__ val mul(val a, val b) { return a * b; }
   static __device__ __forceinline__ val sub(val a, val b) { return a - b; }
@@ -259,6 +260,7 @@ struct PF32 {
   static __device__ __forceinline__ val from_double(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ double to_double(val v) { return (double)v; }
   // scalar helpers of the phi-line ring solve
+  static __device__ __forceinline__ dacc d_of(val v) { return {v, 0.f}; }
   static __device__ __forceinline__ val one() { return 1.f; }
   static __device__ __forceinline__ val mul(val a, val b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ val sub(val a, val b) { return __fsub_rn(a, b); }

@@ -604,14 +604,17 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // ring held in shared memory: every lane runs its contiguous chunk from a
 // zero carry, the chunk maps c -> mu^len c + s are composed across lanes by
 // a shuffle scan, the ring closure gives the carry into every chunk, and a
-// second pass applies the recurrence from the right carry.  Returns (in
-// acc) this lane's share of ||F x||^2; x is overwritten by F^T F x.
+// second pass applies the recurrence from the right carry.  Adds this
+// lane's share of ||F x||^2 to acc (a plain sum in the arithmetic's own
+// type: F x is itself computed in that arithmetic, so a compensated sum of
+// its squares would not be more accurate than the values it sums); x is
+// overwritten by F^T F x.
 // mu_m = mu^m and mu_rem = mu^(n mod m) for the lanes' chunk lengths
 // m = ceil(n / 32) and n mod m; inv = 1 / (1 - mu^n) closes the ring.
 template <class A>
 __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A::val mu,
                                            typename A::val mu_m, typename A::val mu_rem,
-                                           typename A::val inv, typename A::dacc &acc, int lane) {
+                                           typename A::val inv, typename A::val &acc, int lane) {
   using val = typename A::val;
   const int m = (n + 31) >> 5;
   const int a = min(lane * m, n), b = min(a + m, n);
@@ -640,7 +643,7 @@ __device__ __forceinline__ void ring_solve(typename A::val *x, int n, typename A
   for (int k = a; k < b; k++) {
     t = A::fma(mu, t, x[k]);
     x[k] = t;
-    A::d_add(acc, t, t);
+    acc = A::fma(t, t, acc);
   }
   __syncwarp();
   // ---- backward recurrence v_k = u_k + mu v_{k+1}
@@ -848,9 +851,9 @@ __global__ void __launch_bounds__(NT)
         A::d_merge(arr, s[0]);
         if constexpr (LINE) {
           // z = T^-1 r on the ring; rho += (mu / c) ||F r||^2; w = D z
-          typename A::dacc sz = A::d_init();
+          val sz = A::zero();
           ring_solve<A>(xr, np, lmu, lmm, lmr, linv, sz, lane);
-          A::d_addw(arho, wrow, sz);
+          A::d_addw(arho, wrow, A::d_of(sz));
           const size_t ro = cc.off;
           for (int k = lane * V; k < np; k += 32 * V) {
             val wv_[V];
