@@ -94,7 +94,7 @@ def get_threads() -> int:
 
 
 OUTER = {"source": 0, "closed": 1}
-PRECOND = {"jacobi": 0, "rline": 1, "philine": 2}
+PRECOND = {"jacobi": 0, "rline": 1, "philine": 2, "lines": 3}
 
 
 class Grid:
@@ -105,7 +105,8 @@ class Grid:
     ``t_faces`` is given.  ``outer``: "source" (source surface, Phi = 0 at r1)
     or "closed" (closed wall, Br = 0 at r1), Sec. 2.1.  ``precond``: "jacobi"
     (diagonal scaling, PC1 of Sec. 2.3), "rline" (radial-line Jacobi) or
-    "philine" (phi-line Jacobi: one cyclic tridiagonal solve per ring)."""
+    "philine" (phi-line Jacobi: one cyclic tridiagonal solve per ring) or
+    "lines" (both: M^-1 = T_r^-1 + T_phi^-1 - D^-1)."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
                  outer="source", precond="jacobi"):

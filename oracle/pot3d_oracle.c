@@ -82,9 +82,16 @@ static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi line
  *       neighbours); z = M^-1 r is one tridiagonal solve per column;
  *   2 = phi-line Jacobi: M is the part of L that couples cells of one
  *       (r, theta) ring (the full diagonal and the two periodic phi
- *       neighbours); z = M^-1 r is one cyclic tridiagonal solve per ring. */
+ *       neighbours); z = M^-1 r is one cyclic tridiagonal solve per ring;
+ *   3 = both line directions, added: M^-1 = T_r^-1 + T_phi^-1 - D^-1 with
+ *       T_r, T_phi the radial-line and phi-line parts above and D the
+ *       diagonal.  It is symmetric positive definite: scaled by D^1/2 on
+ *       both sides it is I + f(K_r) + f(K_phi), f(K) = K (I - K)^-1, where
+ *       K = D^-1/2 C D^-1/2 holds one line direction's couplings C; the
+ *       eigenvalues l of K lie in (-1, 1), so those of f(K), l / (1 - l),
+ *       exceed -1/2, and the sum stays above 0. */
 int orc_set_precond(int kind) {
-  if (kind < 0 || kind > 2) return 3;
+  if (kind < 0 || kind > 3) return 3;
   g_precond = kind;
   return 0;
 }
@@ -299,36 +306,39 @@ static void cyclic_solve(int n, double dg, double off, const double *d, double *
   for (int i = 0; i < n; i++) x[i] -= f * w[i];
 }
 
-static void precond_apply(const orc_op *op, const double *r, double *z) {
+static void precond_jacobi(const orc_op *op, const double *r, double *z) {
+  const long n = (long)op->nr * op->nt * op->np;
+  const int np = op->np;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < n; c++) z[c] = r[c] / op->diag[c / np];
+}
+
+static void precond_philine(const orc_op *op, const double *r, double *z) {
+  const int nr = op->nr, nt = op->nt, np = op->np;
+#pragma omp parallel
+  {
+    double *work = malloc(sizeof(double) * 7 * (np > 3 ? np : 3));
+#pragma omp for schedule(static)
+    for (long row = 0; row < (long)nr * nt; row++) {
+      const double dg = op->diag[row], off = -op->cp[row];
+      const double *rr = r + row * np;
+      double *zz = z + row * np;
+      if (np == 2) {
+        /* both phi faces couple to the one other cell: [[dg, 2 off], [2 off, dg]] */
+        const double det = dg * dg - 4.0 * off * off;
+        zz[0] = (dg * rr[0] - 2.0 * off * rr[1]) / det;
+        zz[1] = (dg * rr[1] - 2.0 * off * rr[0]) / det;
+      } else {
+        cyclic_solve(np, dg, off, rr, zz, work);
+      }
+    }
+    free(work);
+  }
+}
+
+static void precond_rline(const orc_op *op, const double *r, double *z) {
   const int nr = op->nr, nt = op->nt, np = op->np;
   const long plane = (long)nt * np;
-  if (g_precond == 0) {
-#pragma omp parallel for schedule(static)
-    for (long c = 0; c < (long)nr * plane; c++) z[c] = r[c] / op->diag[c / np];
-    return;
-  }
-  if (g_precond == 2) {
-#pragma omp parallel
-    {
-      double *work = malloc(sizeof(double) * 7 * (np > 3 ? np : 3));
-#pragma omp for schedule(static)
-      for (long row = 0; row < (long)nr * nt; row++) {
-        const double dg = op->diag[row], off = -op->cp[row];
-        const double *rr = r + row * np;
-        double *zz = z + row * np;
-        if (np == 2) {
-          /* both phi faces couple to the one other cell: [[dg, 2 off], [2 off, dg]] */
-          const double det = dg * dg - 4.0 * off * off;
-          zz[0] = (dg * rr[0] - 2.0 * off * rr[1]) / det;
-          zz[1] = (dg * rr[1] - 2.0 * off * rr[0]) / det;
-        } else {
-          cyclic_solve(np, dg, off, rr, zz, work);
-        }
-      }
-      free(work);
-    }
-    return;
-  }
 #pragma omp parallel
   {
     double *cp = malloc(sizeof(double) * nr); /* modified super-diagonal */
@@ -358,6 +368,28 @@ static void precond_apply(const orc_op *op, const double *r, double *z) {
     }
     free(cp);
     free(dp);
+  }
+}
+
+static void precond_apply(const orc_op *op, const double *r, double *z) {
+  if (g_precond == 0) {
+    precond_jacobi(op, r, z);
+  } else if (g_precond == 1) {
+    precond_rline(op, r, z);
+  } else if (g_precond == 2) {
+    precond_philine(op, r, z);
+  } else {
+    /* both line directions: z = T_r^-1 r + T_phi^-1 r - D^-1 r */
+    const long n = (long)op->nr * op->nt * op->np;
+    double *t = malloc(sizeof(double) * n);
+    double *d = malloc(sizeof(double) * n);
+    precond_rline(op, r, z);
+    precond_philine(op, r, t);
+    precond_jacobi(op, r, d);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) z[c] = z[c] + t[c] - d[c];
+    free(t);
+    free(d);
   }
 }
 

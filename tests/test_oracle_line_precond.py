@@ -101,3 +101,54 @@ def test_line_preconditioners_same_solution_fewer_iterations(oracle_mod):
     for x in (xr, xp):
         assert np.linalg.norm(x - xj) / np.linalg.norm(xj) <= 1e-10
     assert itp < 0.6 * itj and itp < itr < itj, (itj, itr, itp)
+
+
+@pytest.mark.parametrize("outer", ["source", "closed"])
+@pytest.mark.parametrize("shape,ratio", [((4, 5, 7), 1.1), ((3, 6, 3), 1.0), ((5, 4, 8), 1.3)])
+def test_precond_both_lines_is_the_additive_combination(oracle_mod, shape, ratio, outer):
+    """Both line directions: M^-1 = T_r^-1 + T_phi^-1 - D^-1 with T_r, T_phi
+    cut out of the dense L; M^-1 is symmetric positive definite."""
+    g = oracle_mod.Grid(*shape, ratio=ratio, outer=outer, precond="lines")
+    A = g.dense()
+    Minv = (np.linalg.inv(line_part(A, shape, "rline")) + np.linalg.inv(line_part(A, shape, "philine"))
+            - np.diag(1.0 / np.diag(A)))
+    np.testing.assert_allclose(Minv, Minv.T, rtol=0, atol=1e-13 * np.abs(Minv).max())
+    assert np.linalg.eigvalsh(0.5 * (Minv + Minv.T)).min() > 0
+    r = syn.random_field(shape, seed=7)
+    z = g.apply_precond(r)
+    zd = Minv @ r.ravel()
+    np.testing.assert_allclose(z.ravel(), zd, rtol=1e-12, atol=1e-13 * np.abs(zd).max())
+
+
+def test_pcg_both_lines_matches_dense_and_first_step(oracle_mod):
+    shape = (4, 5, 6)
+    g = oracle_mod.Grid(*shape, ratio=1.1, precond="lines")
+    A = g.dense()
+    br = syn.random_field((5, 6), seed=11)
+    b = g.rhs(br)
+    x, it, st = g.pcg(b, 1e-13)
+    assert st == oracle_mod.OK
+    xd = np.linalg.solve(A, b.ravel())
+    assert np.linalg.norm(x.ravel() - xd) / np.linalg.norm(xd) < 1e-11
+    Minv = (np.linalg.inv(line_part(A, shape, "rline")) + np.linalg.inv(line_part(A, shape, "philine"))
+            - np.diag(1.0 / np.diag(A)))
+    z = Minv @ b.ravel()
+    alpha = (b.ravel() @ z) / (z @ A @ z)
+    x1, it1, st1 = g.pcg(b, 1e-300, maxit=1)
+    np.testing.assert_allclose(x1.ravel(), alpha * z, rtol=1e-12, atol=1e-14 * np.abs(z).max())
+
+
+def test_both_lines_beat_either_under_strong_radial_stretching(oracle_mod):
+    """With a first radial cell 1000 times thinner than the angular cells
+    the radial couplings dominate almost everywhere and phi lines alone help
+    little; adding radial lines removes that anisotropy as well."""
+    shape, ratio = (41, 31, 61), 1.15
+    br = syn.bipole_br(31, 61, seed=1709, n_bipoles=30)
+    its = {}
+    xs = {}
+    for pc in ("jacobi", "rline", "philine", "lines"):
+        xs[pc], its[pc], st = oracle_mod.Grid(*shape, ratio=ratio, precond=pc).solve(br, 1e-10)
+        assert st == oracle_mod.OK
+    for pc in ("rline", "philine", "lines"):
+        assert np.linalg.norm(xs[pc] - xs["jacobi"]) / np.linalg.norm(xs["jacobi"]) <= 1e-8
+    assert its["lines"] < its["rline"] < its["philine"] < its["jacobi"], its
