@@ -138,7 +138,15 @@ def test_c2_full_solve(p3, oracle_mod, c2, gold, prec, tol):
     rs = np.array(ref["sample_phi"])
     err = np.linalg.norm(xs - rs) / np.linalg.norm(rs)
     # the library's own FP64 residual agrees with the oracle's recomputation
-    assert abs(st["relres_fp64"] - true_rel) <= 0.02 * true_rel
+    # within their rounding: each side evaluates b - A x with per-element
+    # error at most gamma_16 (|b| + |A||x|) (8 terms, coefficients formed in
+    # up to 8 operations).  b is nonzero on the inner layer only, so the
+    # interior rows are pure cancellation and the bound is about 1e-13 here
+    u = 2.0 ** -53
+    ax = np.abs(x)
+    abs_a_x = 2.0 * g.diag()[:, :, None] * ax - g.apply(ax)  # |A| |x|: A = D - C, C >= 0
+    noise = 2.0 * 16 * u / (1 - 16 * u) * np.linalg.norm(np.abs(b) + abs_a_x) / np.linalg.norm(b)
+    assert abs(st["relres_fp64"] - true_rel) <= noise, (st["relres_fp64"], true_rel, noise)
     if prec == "mixed":
         # refinement stops on the FP64 residual itself
         assert true_rel <= tol * 1.0001, true_rel
