@@ -70,6 +70,17 @@ extern "C" {
                                both phi neighbours, periodic): a cyclic tridiagonal
                                solve per ring, the stronger line preconditioner of
                                the kind Sec. 6 calls for.  FP64 and MIXED plans       */
+#define POT3D_PC_R_LINE 2   /* radial-line Jacobi: z = T_r^-1 r with T_r the part of L
+                               inside each radial column (diagonal and both r
+                               neighbours): one tridiagonal solve per (theta, phi)
+                               column.  Radial couplings dominate where the r mesh is
+                               stretched (thin cells near r0).  FP64 and MIXED plans  */
+#define POT3D_PC_LINES 3    /* both line directions, additively:
+                               M^-1 = T_r^-1 + T_phi^-1 - D^-1.  It is SPD: scaled
+                               by D^1/2 on both sides it is I + f(K_r) + f(K_phi),
+                               f(K) = K (I - K)^-1 with K one direction's scaled
+                               couplings (eigenvalues in (-1, 1)), and each f(K) has
+                               eigenvalues above -1/2.  FP64 and MIXED plans          */
 
 /* ---- boundary conditions (Sec. 2.1) ---------------------------------- */
 #define POT3D_OUTER_SOURCE_SURFACE 0 /* Phi = 0 at r = r1                              */
@@ -128,9 +139,11 @@ typedef struct {
                          most 10 restarts, within max_iters in total).  stats
                          report the FP64 residual and the restarts (outer_iters).
                          MIXED always stops on the FP64 residual.                */
-  int precond;        /* POT3D_PC_*: the preconditioner (POT3D_PC_PHI_LINE with FP64
-                         or MIXED plans, and in single solves only: a FP64_DF plan
-                         or a batch submission returns POT3D_ERR_UNSUPPORTED)   */
+  int precond;        /* POT3D_PC_*: the preconditioner.  The line preconditioners
+                         run with FP64 or MIXED plans (a FP64_DF solve returns
+                         POT3D_ERR_UNSUPPORTED); batches take POT3D_PC_JACOBI and
+                         POT3D_PC_PHI_LINE (pot3d_batch_set_opts returns
+                         POT3D_ERR_UNSUPPORTED for the others)                  */
   int history;        /* FP64 and FP64_DF: 1 = record the recurrence residual
                          ||r_k|| / ||b|| of every iteration k = 0 .. iters of the
                          next solves (with verify: of the last restart), read back

@@ -154,6 +154,7 @@ struct PF64 {
   static __device__ __forceinline__ val one() { return 1.0; }
   static __device__ __forceinline__ val mul(val a, val b) { return a * b; }
   static __device__ __forceinline__ val sub(val a, val b) { return a - b; }
+  static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val div(val a, val b) { return a / b; }
   static __device__ __forceinline__ val shfl_up(val v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
   static __device__ __forceinline__ val shfl_down(val v, int d) {
@@ -264,6 +265,7 @@ struct PF32 {
   static __device__ __forceinline__ val one() { return 1.f; }
   static __device__ __forceinline__ val mul(val a, val b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ val sub(val a, val b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ val add(val a, val b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ val div(val a, val b) { return __fdiv_rn(a, b); }
   static __device__ __forceinline__ val shfl_up(val v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
   static __device__ __forceinline__ val shfl_down(val v, int d) {

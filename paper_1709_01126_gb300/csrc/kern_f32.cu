@@ -15,6 +15,9 @@ KLaunch update_launcher_f32() { return &up_launch<PF32, kUpdThreadsF32, kUpdSegB
 KLineLaunch update_line_launcher_f32() {
   return &up_line_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>;
 }
+KRLaunch rline_launcher_f32(bool add) {
+  return add ? &rl_launch<PF32, true> : &rl_launch<PF32, false>;
+}
 int update_occupancy_f32() { return up_occupancy<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>(); }
 
 // Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
@@ -41,6 +44,13 @@ KLineLaunch update_line_launcher_f64();
 KLineLaunch update_line_launcher(int ai) {
   if (ai == 0) return update_line_launcher_f64();
   if (ai == 2) return update_line_launcher_f32();
+  return nullptr;
+}
+
+KRLaunch rline_launcher_f64(bool add);
+KRLaunch rline_launcher(int ai, bool add) {
+  if (ai == 0) return rline_launcher_f64(add);
+  if (ai == 2) return rline_launcher_f32(add);
   return nullptr;
 }
 

@@ -14,6 +14,9 @@ KLaunch update_launcher_f64() { return &up_launch<PF64, kUpdThreadsF64, kUpdSegB
 KLineLaunch update_line_launcher_f64() {
   return &up_line_launch<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>;
 }
+KRLaunch rline_launcher_f64(bool add) {
+  return add ? &rl_launch<PF64, true> : &rl_launch<PF64, false>;
+}
 int update_occupancy_f64() { return up_occupancy<PF64, kUpdThreadsF64, kUpdSegBytes, kUpdStagesF64>(); }
 
 } // namespace pot3d

@@ -89,6 +89,12 @@ int up_line_launch(const ProbDev *probs, const int2 *work, const int *nwork, int
   return 0;
 }
 
+// Radial-line kernel: one block per tiles_c work item, no dynamic shared memory.
+template <class A, bool ADD>
+void rl_launch(const ProbDev *probs, int grid, double *setup_out, cudaStream_t s) {
+  k_rline<A, kRLineThreads, ADD><<<grid, kRLineThreads, 0, s>>>(probs, setup_out);
+}
+
 // resident blocks of the update kernel per SM (0 if the query fails)
 template <class A, int NT, int SEGB, int STG>
 int up_occupancy() {

@@ -50,6 +50,7 @@ struct SolveState {
   double sigma;    // last p.Ap
   double scale;    // power-of-two scale applied to b
   double rr;       // ||r_k||^2 as summed by the update kernel
+  double rho_part; // both line directions: the phi-line update's share of rho
   int iter;        // completed iterations
   int maxit;
   int status;
@@ -85,9 +86,15 @@ struct ProbDev {
   double *hist;       // residual history [hist_cap] (null: not recorded)
   int hist_cap;
   int pad2_;
-  void *w;            // phi-line preconditioner: w = D M^-1 r (null: PC1)
+  void *w;            // line preconditioners: w = D M^-1 r (null: PC1)
   const void *lcoef;  // phi-line table [6][nr][ntp]: mu, mu / c, D mu / c, mu^m,
                       // mu^(np mod m), 1 / (1 - mu^np)  (m = ceil(np / 32))
+  const void *rcoef;  // radial-line table [4][nr][ntp]: l, 1 / d', D / d', l' D / D'
+                      // (see k_rline; null: no radial lines)
+  double *part_c;     // [2 * tiles_c] partials of the radial-line kernel
+  int tiles_c;        // radial-line blocks (8 warps of 32 columns each)
+  int lines;          // 1: both line directions (the phi-line update forms
+                      // w - r and leaves the close of the iteration to k_rline)
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -687,6 +694,27 @@ struct UpLayout {
   static constexpr int BYTES = NW * WARP_BYTES + NW * STG * 8;
 };
 
+// Closes iteration kit of a problem (one thread): relative residual,
+// history, status, and for a running solve beta_k and rho_k.
+__device__ __forceinline__ void close_iteration(const ProbDev &P, SolveState *stt, int kit,
+                                                double rr, double rho) {
+  const double relres = sqrt(rr) / sqrt(stt->bb);
+  stt->relres = relres;
+  stt->rr = rr;
+  stt->iter = kit;
+  if (P.hist && kit < P.hist_cap) P.hist[kit] = relres;
+  if (!isfinite(relres)) {
+    stt->status = ST_BREAKDOWN;
+  } else if (relres <= stt->tol) {
+    stt->status = ST_CONVERGED;
+  } else if (kit >= stt->maxit) {
+    stt->status = ST_MAXIT;
+  } else {
+    stt->beta[kit & 1] = rho / stt->rho;
+    stt->rho = rho;
+  }
+}
+
 // Work item = (problem, block of rows_b phi rows).  Each warp walks its rows
 // (row0 + warp, + NW, ...) in segments of at most SEGB bytes: lane 0 keeps
 // STG - 1 segments of r and q in flight ahead of the one the warp computes
@@ -801,7 +829,8 @@ __global__ void __launch_bounds__(NT)
     int issued = 0;
     for (; issued < min(units, STG - 1); issued++) issue(issued);
     int u = 0;
-    coef wrow{}, lmu{}, lgd{}, lmm{}, lmr{}, linv{};
+    coef wrow{}, lmu{}, lgd{}, lmm{}, lmr{}, linv{}, ldinv{};
+    const bool lines = LINE && P.lines;
     for (; u < units; u++) {
       if (issued < units) issue(issued++);
       if (cc.seg == 0) { // ahead of the wait
@@ -813,6 +842,7 @@ __global__ void __launch_bounds__(NT)
           lmm = lc[3 * RT + rj];
           lmr = lc[4 * RT + rj];
           linv = lc[5 * RT + rj];
+          if (lines) ldinv = cf[rj];
         } else {
           wrow = cf[rj];
         }
@@ -855,11 +885,24 @@ __global__ void __launch_bounds__(NT)
           ring_solve<A>(xr, np, lmu, lmm, lmr, linv, sz, lane);
           A::d_addw(arho, wrow, A::d_of(sz));
           const size_t ro = cc.off;
-          for (int k = lane * V; k < np; k += 32 * V) {
-            val wv_[V];
+          if (lines) {
+            // both directions: this kernel's share is T_phi^-1 - D^-1
+            // (rho -= D^-1 r.r on the row; w = D z - r, with r as this
+            // lane stored it above)
+            A::d_addw(arho, -ldinv, s[0]);
+            for (int k = lane * V; k < np; k += 32 * V) {
+              val wv_[V];
 #pragma unroll
-            for (int e = 0; e < V; e++) wv_[e] = A::mul(lgd, xr[k + e]);
-            A::stvv(wv + ro + k, wv_);
+              for (int e = 0; e < V; e++) wv_[e] = A::sub(A::mul(lgd, xr[k + e]), A::ld(r + ro + k + e));
+              A::stvv(wv + ro + k, wv_);
+            }
+          } else {
+            for (int k = lane * V; k < np; k += 32 * V) {
+              val wv_[V];
+#pragma unroll
+              for (int e = 0; e < V; e++) wv_[e] = A::mul(lgd, xr[k + e]);
+              A::stvv(wv + ro + k, wv_);
+            }
           }
           __syncwarp();
         } else {
@@ -905,26 +948,183 @@ __global__ void __launch_bounds__(NT)
         continue;
       }
       if (tid == 0) {
-        const double relres = sqrt(rr) / sqrt(stt->bb);
-        stt->relres = relres;
-        stt->rr = rr;
-        stt->iter = kit;
-        if (P.hist && kit < P.hist_cap) P.hist[kit] = relres;
-        if (!isfinite(relres)) {
-          stt->status = ST_BREAKDOWN;
-        } else if (relres <= stt->tol) {
-          stt->status = ST_CONVERGED;
-        } else if (kit >= stt->maxit) {
-          stt->status = ST_MAXIT;
+        if (LINE && P.lines) {
+          // both line directions: k_rline adds the radial share and closes
+          stt->rr = rr;
+          stt->rho_part = rho;
         } else {
-          stt->beta[kit & 1] = rho / stt->rho;
-          stt->rho = rho;
+          close_iteration(P, stt, kit, rr, rho);
         }
         stt->ticket_b = 0u;
         __threadfence();
       }
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ radial lines
+// Radial-line Jacobi (Sec. 6 names stronger preconditioners that still
+// vectorise as the open direction; this is the line counterpart of PC1 in r):
+// M = T_r, the part of L inside each radial column (j, k): the full
+// diagonal D_i (= D_ij) and the couplings e_i = -c^r_{i+1/2,j} between
+// cells i and i + 1.  T_r is symmetric, diagonally dominant and the same for
+// every k of a theta row, so its factorisation T_r = L' diag(d') L'^T
+// (L' unit lower bidiagonal, multipliers l_i = e_{i-1} / d'_{i-1},
+// d'_i = D_i - e_{i-1} l_i) is a table per (i, j), and a solve is two
+// first-order recurrences along the column:
+//     y_i = r_i - l_i y_{i-1}                       (forward, L'^-1)
+//     z_i = y_i / d'_i - l_{i+1} z_{i+1}            (backward, L'^-T diag(d')^-1)
+// and rho = r . T_r^-1 r = sum_i y_i^2 / d'_i.  In the scaled iteration the
+// kernel writes w = D z; the backward recurrence runs on w directly:
+//     w_i = (D_i / d'_i) y_i - (l_{i+1} D_i / D_{i+1}) w_{i+1}.
+// Table [4][nr][ntp]: l_i, 1 / d'_i, D_i / d'_i, l_{i+1} D_i / D_{i+1}.
+//
+// One thread per column, 32 adjacent phi columns of one theta row per warp
+// (every row access of the warp is one contiguous segment), 8 warps per
+// block.  The forward pass keeps y in q's storage (q is dead once r is
+// updated; the next matvec rewrites it), the backward pass reads it back in
+// reverse order (mostly from L2).  ADD = false: the kernel is the whole
+// update of the iteration (r -= alpha q, ||r||^2, radial-line rho, w) and
+// closes it.  ADD = true (both line directions): the phi-line update ran
+// first (r updated, w holds D (T_phi^-1 - D^-1) r, ||r||^2 and its rho
+// share in the state); this kernel adds D T_r^-1 r to w and the radial
+// share to rho, and closes the iteration.  setup_out non-null: alpha = 0,
+// no iteration is closed; the last block writes ||r||^2 and rho to
+// setup_out[0..1] (ADD: adds the radial share to setup_out[1]).
+template <class A, int NT, bool ADD>
+__global__ void __launch_bounds__(NT)
+    k_rline(const ProbDev *__restrict__ probs, double *setup_out) {
+  using val = typename A::val;
+  using st = typename A::st;
+  using coef = typename A::coef;
+  constexpr int NW = NT / 32, PF = 4;
+  __shared__ double red[NW];
+  __shared__ int s_last;
+  const ProbDev &P = probs[0];
+  SolveState *stt = P.st;
+  const bool setup = setup_out != nullptr;
+  if (!setup && ldcg(&stt->status) != ST_RUNNING) return;
+  const int kit = ldcg(&stt->iter) + 1;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, tid = threadIdx.x;
+  const int nr = P.nr, nt = P.nt, np = P.np, ntp = P.ntp;
+  const size_t plane = (size_t)P.plane;
+  const size_t RT = (size_t)nr * ntp;
+  const int nkg = (np + 31) >> 5;
+  const int t = blockIdx.x;
+  const int u = t * NW + wy;
+  typename A::dacc arr = A::d_init(), arho = A::d_init();
+  if (u < nt * nkg) {
+    const int j = u / nkg;
+    const int k = (u - j * nkg) * 32 + lane;
+    if (k < np) {
+      st *__restrict__ r = static_cast<st *>(P.r);
+      st *__restrict__ q = static_cast<st *>(P.q); // y scratch after the r update
+      st *__restrict__ w = static_cast<st *>(P.w);
+      const coef *__restrict__ tl = static_cast<const coef *>(P.rcoef) + j;
+      const typename A::scal nalpha =
+          A::scal_from((ADD || setup) ? 0.0 : -ldcg(&stt->alpha[kit & 1]));
+      const size_t c0 = (size_t)j * P.pitch + k;
+      // ---- forward: r update, ||r||^2, y, rho
+      val y = A::zero();
+      int i = 0;
+      for (; i + PF <= nr; i += PF) {
+        val rv[PF], qv[PF];
+#pragma unroll
+        for (int e = 0; e < PF; e++) {
+          rv[e] = A::ld(r + c0 + (size_t)(i + e) * plane);
+          qv[e] = ADD ? A::zero() : A::ld(q + c0 + (size_t)(i + e) * plane);
+        }
+#pragma unroll
+        for (int e = 0; e < PF; e++) {
+          const size_t o = c0 + (size_t)(i + e) * plane;
+          if (!ADD) {
+            rv[e] = A::fma(nalpha, qv[e], rv[e]);
+            if (!setup) A::stv(r + o, rv[e]);
+            A::d_add(arr, rv[e], rv[e]);
+          }
+          const coef l = __ldg(tl + (size_t)(i + e) * ntp);
+          const coef id = __ldg(tl + RT + (size_t)(i + e) * ntp);
+          y = A::fma(-l, y, rv[e]);
+          A::stv(q + o, y);
+          A::d_add(arho, y, A::mul(id, y));
+        }
+      }
+      for (; i < nr; i++) {
+        const size_t o = c0 + (size_t)i * plane;
+        val rv = A::ld(r + o);
+        if (!ADD) {
+          rv = A::fma(nalpha, A::ld(q + o), rv);
+          if (!setup) A::stv(r + o, rv);
+          A::d_add(arr, rv, rv);
+        }
+        const coef l = __ldg(tl + (size_t)i * ntp);
+        const coef id = __ldg(tl + RT + (size_t)i * ntp);
+        y = A::fma(-l, y, rv);
+        A::stv(q + o, y);
+        A::d_add(arho, y, A::mul(id, y));
+      }
+      // ---- backward: w = D z (ADD: plus the phi-line share already in w)
+      val wn = A::zero();
+      i = nr - 1;
+      for (; i + 1 >= PF; i -= PF) {
+        val yv[PF], av[PF];
+#pragma unroll
+        for (int e = 0; e < PF; e++) {
+          yv[e] = A::ld(q + c0 + (size_t)(i - e) * plane);
+          av[e] = ADD ? A::ld(w + c0 + (size_t)(i - e) * plane) : A::zero();
+        }
+#pragma unroll
+        for (int e = 0; e < PF; e++) {
+          const size_t ti = (size_t)(i - e) * ntp;
+          const coef g = __ldg(tl + 2 * RT + ti);
+          const coef h = __ldg(tl + 3 * RT + ti);
+          wn = A::fma(-h, wn, A::mul(g, yv[e]));
+          val out = wn;
+          if constexpr (ADD) out = A::add(wn, av[e]);
+          A::stv(w + c0 + (size_t)(i - e) * plane, out);
+        }
+      }
+      for (; i >= 0; i--) {
+        const size_t o = c0 + (size_t)i * plane;
+        const coef g = __ldg(tl + 2 * RT + (size_t)i * ntp);
+        const coef h = __ldg(tl + 3 * RT + (size_t)i * ntp);
+        wn = A::fma(-h, wn, A::mul(g, A::ld(q + o)));
+        val out = wn;
+        if constexpr (ADD) out = A::add(wn, A::ld(w + o));
+        A::stv(w + o, out);
+      }
+    }
+  }
+  const double prr = ADD ? 0.0 : block_sum<NT>(A::d_get(arr), red);
+  const double prho = block_sum<NT>(A::d_get(arho), red);
+  if (tid == 0) {
+    P.part_c[2 * t] = prr;
+    P.part_c[2 * t + 1] = prho;
+    __threadfence();
+    const unsigned prev = atomicAdd(&stt->ticket_b, 1u);
+    s_last = (prev == (unsigned)(P.tiles_c - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double rr = ADD ? 0.0 : block_sum_array<NT>(P.part_c, P.tiles_c, 2, red);
+  const double rho_r = block_sum_array<NT>(P.part_c + 1, P.tiles_c, 2, red);
+  if (tid == 0) {
+    if (setup) {
+      if (ADD) {
+        setup_out[1] += rho_r;
+      } else {
+        setup_out[0] = rr;
+        setup_out[1] = rho_r;
+      }
+    } else if (ADD) {
+      close_iteration(P, stt, kit, ldcg(&stt->rr), rho_r + ldcg(&stt->rho_part));
+    } else {
+      close_iteration(P, stt, kit, rr, rho_r);
+    }
+    stt->ticket_b = 0u;
+    __threadfence();
   }
 }
 

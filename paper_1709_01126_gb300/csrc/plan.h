@@ -26,7 +26,10 @@ struct ArithData {
   int *d_nwork = nullptr; // [tiles_a, tiles_b]
   void *coef = nullptr; // scaled metric table [6][nr][ntp] in the arithmetic's type
   void *lcoef = nullptr; // phi-line table [6][nr][ntp] (see ensure_line)
-  bool graph_line = false; // the captured graph launches the phi-line update
+  void *rcoef = nullptr; // radial-line table [4][nr][ntp] (see ensure_rline)
+  double *part_c = nullptr; // [2 * tiles_c] radial-line partials
+  int tiles_c = 0;
+  int graph_pc = 0; // the preconditioner the captured graph launches (POT3D_PC_*)
   ProbDev *d_prob = nullptr;
   SolveState *d_state = nullptr;
   double *part_a = nullptr, *part_b = nullptr;
@@ -78,7 +81,8 @@ struct Plan {
   int nsm = 0;
   std::vector<cudaEvent_t> ev;
   bool freeze_poll = false; // testing hook: the host re-reads a stale state snapshot
-  bool line = false;         // the solve in progress uses the phi-line preconditioner
+  bool line = false;         // the solve in progress runs the phi-line update
+  bool rline = false;        // the solve in progress runs the radial-line kernel
   double *d_hist = nullptr;  // residual history of the last PCG run (opts.history)
   int hist_alloc = 0, hist_n = 0;
 };
@@ -91,6 +95,10 @@ void plan_free(Plan *P);
 int ensure_arith(Plan *P, int ai);
 // phi-line table of arithmetic ai (AR_F64 or AR_F32), built on first use
 int ensure_line(Plan *P, int ai);
+// radial-line table and partials of arithmetic ai (AR_F64 or AR_F32), built on first use
+int ensure_rline(Plan *P, int ai);
+// radial-line blocks of a plan (8 warps of 32 phi columns of one theta row)
+int rline_tiles(const Plan *P);
 size_t workspace_bytes(const Plan *P);
 int ensure_workspace(Plan *P);
 void *ws_vec(const Plan *P, int v, size_t es);

@@ -274,12 +274,69 @@ int ensure_line(Plan *P, int ai) {
   return rc;
 }
 
+// Radial-line table: per theta row j, the tridiagonal T_r of every radial
+// column (diagonal D_i, couplings e_i = -c^r_{i+1/2} between i and i + 1;
+// e_{nr-1} = 0: the outer face is a boundary face) factored as
+// L' diag(d') L'^T: l_i = e_{i-1} / d'_{i-1}, d'_i = D_i - e_{i-1} l_i.
+// The kernel needs l_i, 1 / d'_i (rho), D_i / d'_i and
+// l_{i+1} D_i / D_{i+1} (w = D z directly).  Layout [4][nr][ntp].
+int rline_tiles(const Plan *P) {
+  const long units = (long)P->nt * ((P->np + 31) / 32);
+  return (int)((units + kRLineThreads / 32 - 1) / (kRLineThreads / 32));
+}
+
+int ensure_rline(Plan *P, int ai) {
+  ArithData &A = P->ar[ai];
+  const int tiles = rline_tiles(P);
+  if (A.tiles_c < tiles) {
+    cudaFree(A.part_c);
+    A.part_c = nullptr;
+    A.tiles_c = 0;
+    if (cudaMalloc(&A.part_c, sizeof(double) * 2 * tiles) != cudaSuccess) {
+      cudaGetLastError();
+      return POT3D_ERR_OOM;
+    }
+    A.tiles_c = tiles;
+  }
+  if (A.rcoef) return POT3D_OK;
+  const int nr = P->nr, nt = P->nt, ntp = P->ntp;
+  const size_t R = P->R, RP = (size_t)nr * ntp;
+  std::vector<double> t(4 * RP, 0.0);
+  for (int j = 0; j < nt; j++) {
+    double dprev = 0.0;
+    for (int i = 0; i < nr; i++) {
+      const size_t row = (size_t)i * nt + j, o = (size_t)i * ntp + j;
+      const double D = P->c64h[C64_D * R + row];
+      const double e = i > 0 ? -P->c64h[C64_RP * R + row - nt] : 0.0;
+      const double l = i > 0 ? e / dprev : 0.0;
+      const double dp = D - e * l;
+      t[o] = l;
+      t[RP + o] = 1.0 / dp;
+      t[2 * RP + o] = D / dp;
+      dprev = dp;
+    }
+    for (int i = 0; i + 1 < nr; i++) {
+      const size_t row = (size_t)i * nt + j, o = (size_t)i * ntp + j;
+      t[3 * RP + o] = t[o + ntp] * P->c64h[C64_D * R + row] / P->c64h[C64_D * R + row + nt];
+    }
+  }
+  int rc;
+  if (ai == AR_F64) {
+    rc = upload((double **)&A.rcoef, t);
+  } else {
+    std::vector<float> h(t.size());
+    for (size_t u = 0; u < t.size(); u++) h[u] = (float)t[u];
+    rc = upload((float **)&A.rcoef, h);
+  }
+  return rc;
+}
+
 // ----------------------------------------------------------- workspace
-// Vectors: x~, r, p~0, p~1, q and, with the phi-line preconditioner, w in
+// Vectors: x~, r, p~0, p~1, q and, with a line preconditioner, w in
 // the iteration's arithmetic; x64, r64 in FP64 for refinement.
 size_t workspace_bytes(const Plan *P) {
   const size_t v8 = align256(P->npad * 8), v4 = align256(P->npad * 4);
-  const int nv = P->opts.precond == POT3D_PC_PHI_LINE ? 6 : 5;
+  const int nv = P->opts.precond != POT3D_PC_JACOBI ? 6 : 5;
   const size_t f64 = nv * v8;
   const size_t mixed = nv * v4 + 2 * v8;
   return P->prec == POT3D_PREC_MIXED ? mixed : std::max(f64, mixed);
@@ -303,7 +360,7 @@ int ensure_workspace(Plan *P) {
 // Vector v (0..4: x~, r, p~0, p~1, q; 5: w) of an arithmetic with element
 // size es; FP64 refinement vectors x64, r64 follow the FP32 vectors.
 void *ws_vec(const Plan *P, int v, size_t es) { return P->ws + v * align256(P->npad * es); }
-static int n_iter_vecs(const Plan *P) { return P->opts.precond == POT3D_PC_PHI_LINE ? 6 : 5; }
+static int n_iter_vecs(const Plan *P) { return P->opts.precond != POT3D_PC_JACOBI ? 6 : 5; }
 double *ws_x64(const Plan *P) {
   return (double *)(P->ws + n_iter_vecs(P) * align256(P->npad * 4));
 }
@@ -416,7 +473,7 @@ int pot3d_set_stream(pot3d_plan_t *plan, void *s) {
 int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *o) {
   if (!plan || !o) return fail(POT3D_ERR_INVALID_ARG);
   if (o->max_iters < 0 || o->chunk < 0 || o->inner_tol < 0 || !(o->inner_tol < 1.0) ||
-      o->max_outer < 0 || o->verify < 0 || o->verify > 1 || o->precond < 0 || o->precond > 1 ||
+      o->max_outer < 0 || o->verify < 0 || o->verify > 1 || o->precond < 0 || o->precond > 3 ||
       o->history < 0 || o->history > 1)
     return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);

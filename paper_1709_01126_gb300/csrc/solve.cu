@@ -74,6 +74,9 @@ void plan_free(Plan *P) {
     cudaFree(A.d_state);
     cudaFree(A.part_a);
     cudaFree(A.part_b);
+    cudaFree(A.part_c);
+    cudaFree(A.lcoef);
+    cudaFree(A.rcoef);
     cudaFree(A.d_tma);
     cudaFree(A.d_work_a);
     cudaFree(A.d_work_b);
@@ -188,26 +191,60 @@ static void launch_matvec(Plan *P, int ai) {
   v.launch(D.d_prob, D.d_work_a, D.d_nwork, D.tiles_a, P->stream);
 }
 
+// The update step of an iteration per preconditioner: PC1 and phi lines run
+// the update kernel; radial lines the column kernel alone (it is the whole
+// update); both directions the phi-line update (forming D (T_phi^-1 - D^-1) r)
+// and then the column kernel, which adds D T_r^-1 r and closes the iteration.
+static int update_launches(const Plan *P) { return (P->line && P->rline) ? 2 : 1; }
+
 static void launch_update(Plan *P, int ai) {
   ArithData &D = P->ar[ai];
   if (P->line) {
     // the shared memory fits: checked by line_setup before the solve
     update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, nullptr,
                              P->stream);
+    if (P->rline) rline_launcher(ai, true)(D.d_prob, D.tiles_c, nullptr, P->stream);
+    return;
+  }
+  if (P->rline) {
+    rline_launcher(ai, false)(D.d_prob, D.tiles_c, nullptr, P->stream);
     return;
   }
   update_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->stream);
 }
 
-// Phi-line start of a PCG run (solve or refinement step): the update kernel
-// in its setup mode on the current r (alpha = 0) writes w = D T^-1 r for the
-// first matvec and ||r||^2, r.T^-1 r to sums[0..1].
+// The preconditioner of the next PCG run (from the options): which update
+// kernels run, and their tables.
+static int select_precond(Plan *P, int ai) {
+  const int pc = P->opts.precond;
+  P->line = pc == POT3D_PC_PHI_LINE || pc == POT3D_PC_LINES;
+  P->rline = pc == POT3D_PC_R_LINE || pc == POT3D_PC_LINES;
+  if (P->line) {
+    if (!update_line_launcher(ai)) return POT3D_ERR_UNSUPPORTED;
+    TRY(ensure_line(P, ai));
+  }
+  if (P->rline) {
+    if (!rline_launcher(ai, false)) return POT3D_ERR_UNSUPPORTED;
+    TRY(ensure_rline(P, ai));
+  }
+  return POT3D_OK;
+}
+
+// Start of a PCG run with a line preconditioner (solve or refinement step):
+// the kernels in their setup mode on the current r (alpha = 0) write
+// w = D M^-1 r for the first matvec and ||r||^2, r.M^-1 r to sums[0..1].
 static int line_setup(Plan *P, int ai, double *sums) {
   ArithData &D = P->ar[ai];
-  if (update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, sums,
-                               P->stream) != 0)
-    return POT3D_ERR_UNSUPPORTED; // the rings do not fit in shared memory
-  P->stats.launches += 1;
+  if (P->line) {
+    if (update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, sums,
+                                 P->stream) != 0)
+      return POT3D_ERR_UNSUPPORTED; // the rings do not fit in shared memory
+    P->stats.launches += 1;
+  }
+  if (P->rline) {
+    rline_launcher(ai, P->line)(D.d_prob, D.tiles_c, sums, P->stream);
+    P->stats.launches += 1;
+  }
   return POT3D_OK;
 }
 
@@ -325,7 +362,8 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
     // while chunk N+1 runs, so the GPU does not idle on the round trip.  A
     // chunk queued after the solve stopped does nothing (its kernels see the
     // status and exit).
-    if (graphs && (!D.graph || D.graph_chunk != chunk || D.graph_line != P->line)) {
+    const int pc_key = (P->line ? 1 : 0) | (P->rline ? 2 : 0);
+    if (graphs && (!D.graph || D.graph_chunk != chunk || D.graph_pc != pc_key)) {
       if (D.graph) cudaGraphExecDestroy(D.graph);
       D.graph = nullptr;
       cudaGraph_t g;
@@ -339,7 +377,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
       cudaGraphDestroy(g);
       CTRY(e);
       D.graph_chunk = chunk;
-      D.graph_line = P->line;
+      D.graph_pc = pc_key;
     }
     SolveState *snap[2] = {P->h_state, P->h_state + 1};
     auto enqueue = [&](int b) -> int {
@@ -352,7 +390,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
         }
       }
       CTRY(cudaGetLastError());
-      P->stats.launches += 2LL * chunk;
+      P->stats.launches += (1LL + update_launches(P)) * chunk;
       CTRY(cudaMemcpyAsync(snap[b], D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                            P->stream));
       CTRY(cudaEventRecord(P->poll_ev[b], P->stream));
@@ -396,7 +434,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
       CTRY(cudaEventRecord(P->ev[3 * c + 2], P->stream));
     }
     CTRY(cudaGetLastError());
-    P->stats.launches += 2LL * chunk;
+    P->stats.launches += (1LL + update_launches(P)) * chunk;
     CTRY(cudaMemcpyAsync(P->h_state, D.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                          P->stream));
     CTRY(cudaStreamSynchronize(P->stream));
@@ -454,7 +492,11 @@ static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, voi
   h.part_b = D.part_b;
   h.st = D.d_state;
   h.w = w;
-  h.lcoef = w ? D.lcoef : nullptr;
+  h.lcoef = P->line ? D.lcoef : nullptr;
+  h.rcoef = P->rline ? D.rcoef : nullptr;
+  h.part_c = D.part_c;
+  h.tiles_c = D.tiles_c;
+  h.lines = (P->line && P->rline) ? 1 : 0;
 }
 
 static int status_code(int st) {
@@ -536,11 +578,7 @@ static int stage_io(Plan *P, const double *br, double *phi, double *B, bool phi_
 template <class A>
 static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi, int *iters) {
   TRY(ensure_arith(P, ai));
-  P->line = P->opts.precond == POT3D_PC_PHI_LINE;
-  if (P->line) {
-    if (!update_line_launcher(ai)) return fail(POT3D_ERR_UNSUPPORTED);
-    TRY(ensure_line(P, ai));
-  }
+  TRY(select_precond(P, ai));
   TRY(ensure_workspace(P));
   const bool x0 = P->opts.use_x0 != 0;
   Io io;
@@ -548,7 +586,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   const size_t es = sizeof(typename A::st);
   void *x = ws_vec(P, 0, es), *r = ws_vec(P, 1, es), *p0 = ws_vec(P, 2, es),
        *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
-  void *w = P->line ? ws_vec(P, 5, es) : nullptr;
+  void *w = (P->line || P->rline) ? ws_vec(P, 5, es) : nullptr;
   ArithData &D = P->ar[ai];
   fill_prob<A>(P, ai, x, r, p0, p1, q, w);
   TRY(build_tma(P, ai));
@@ -557,7 +595,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   prepare_br(P, io.br, P->d_br_last, P->d_part, P->d_sums + 6, s);
   const double *brs = P->d_br_last;
   P->have_br = true;
-  CTRY(cudaMemsetAsync(P->ws, 0, (P->line ? 6 : 5) * ((P->npad * es + 255) & ~(size_t)255), s));
+  CTRY(cudaMemsetAsync(P->ws, 0, (w ? 6 : 5) * ((P->npad * es + 255) & ~(size_t)255), s));
   const size_t n0 = (size_t)P->nt * P->np;
   const int gb = aux_grid(P, n0);
   k_bstats<kAuxThreads><<<gb, kAuxThreads, 0, s>>>(brs, P->d_S, P->d_c64, P->nr, P->nt, P->np,
@@ -603,8 +641,8 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   }
   CTRY(cudaGetLastError());
   memset(&P->stats, 0, sizeof(P->stats));
-  if (P->line) {
-    // w_0 = D T^-1 r_0 and rho_0 = r_0 . T^-1 r_0 (scaled units)
+  if (w) {
+    // w_0 = D M^-1 r_0 and rho_0 = r_0 . M^-1 r_0 (scaled units)
     TRY(line_setup(P, ai, P->d_sums + 4));
     k_set_rho<<<1, 1, 0, s>>>(D.d_state, P->d_sums + 4);
     P->stats.launches += 1;
@@ -644,8 +682,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
 static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *outer,
                        int *inner) {
   TRY(ensure_arith(P, AR_F32));
-  P->line = P->opts.precond == POT3D_PC_PHI_LINE;
-  if (P->line) TRY(ensure_line(P, AR_F32));
+  TRY(select_precond(P, AR_F32));
   TRY(ensure_workspace(P));
   const bool x0 = P->opts.use_x0 != 0;
   Io io;
@@ -654,7 +691,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   ArithData &D = P->ar[AR_F32];
   void *x = ws_vec(P, 0, 4), *r = ws_vec(P, 1, 4), *p0 = ws_vec(P, 2, 4), *p1 = ws_vec(P, 3, 4),
        *q = ws_vec(P, 4, 4);
-  void *w = P->line ? ws_vec(P, 5, 4) : nullptr;
+  void *w = (P->line || P->rline) ? ws_vec(P, 5, 4) : nullptr;
   double *x64 = ws_x64(P), *r64 = ws_r64(P);
   fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q, w);
   TRY(build_tma(P, AR_F32));
@@ -664,7 +701,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   const double *brs = P->d_br_last;
   P->have_br = true;
   const size_t v4 = (P->npad * 4 + 255) & ~(size_t)255;
-  CTRY(cudaMemsetAsync(P->ws, 0, (P->line ? 6 : 5) * v4, s));
+  CTRY(cudaMemsetAsync(P->ws, 0, (w ? 6 : 5) * v4, s));
   CTRY(cudaMemsetAsync(x64, 0, P->npad * 8, s));
   CTRY(cudaMemsetAsync(r64, 0, P->npad * 8, s));
   if (x0)
@@ -714,8 +751,8 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
     k_inner_rhs<kAuxThreads><<<gn, kAuxThreads, 0, s>>>(r64, dinv32, P->nr, P->nt, P->ntp, P->np,
                                                         P->pitch, new_scale, (float *)r, P->d_part);
     k_sum_pairs<kAuxThreads><<<1, kAuxThreads, 0, s>>>(P->d_part, gn, P->d_sums + 4);
-    // phi lines: w = D T^-1 r32 and rho = r32 . T^-1 r32 replace the sums
-    if (P->line) TRY(line_setup(P, AR_F32, P->d_sums + 4));
+    // line preconditioners: w = D M^-1 r32 and rho = r32 . M^-1 r32 replace the sums
+    if (w) TRY(line_setup(P, AR_F32, P->d_sums + 4));
     CTRY(cudaMemsetAsync(x, 0, v4, s));
     int iter0 = 0;
     if (resumable && !restart) {
@@ -995,6 +1032,7 @@ int tune_arith(Plan *P, int ai, TuneVal *best) {
   TRY(ensure_arith(P, ai));
   TRY(ensure_workspace(P));
   P->line = false; // the tuner times the diagonal-scaling kernels
+  P->rline = false;
   ArithData &D = P->ar[ai];
   const size_t es = sizeof(typename A::st);
   cudaStream_t s = P->stream;

@@ -33,6 +33,13 @@ KLaunch update_launcher(int ai);
 using KLineLaunch = int (*)(const ProbDev *, const int2 *, const int *, int grid, int pitch,
                             double *setup_out, cudaStream_t);
 KLineLaunch update_line_launcher(int ai);
+// The radial-line kernel (FP64 and FP32 only; null for double-float).
+// add = false: the whole update of the iteration with radial lines;
+// add = true: the radial share after the phi-line update (both directions).
+// setup_out non-null: the setup mode at the start of a PCG run.
+using KRLaunch = void (*)(const ProbDev *, int grid, double *setup_out, cudaStream_t);
+KRLaunch rline_launcher(int ai, bool add);
+constexpr int kRLineThreads = 256;
 // resident blocks per SM of arithmetic ai's update kernel (0: unknown)
 int update_occupancy(int ai);
 

@@ -37,7 +37,10 @@ PRECISIONS = {"fp64": POT3D_PREC_FP64, "df": POT3D_PREC_FP64_DF, "mixed": POT3D_
 OUTER = {"source": POT3D_OUTER_SOURCE_SURFACE, "closed": POT3D_OUTER_CLOSED_WALL}
 POT3D_PC_JACOBI = 0
 POT3D_PC_PHI_LINE = 1
-PRECONDS = {"jacobi": POT3D_PC_JACOBI, "philine": POT3D_PC_PHI_LINE}
+POT3D_PC_R_LINE = 2
+POT3D_PC_LINES = 3
+PRECONDS = {"jacobi": POT3D_PC_JACOBI, "philine": POT3D_PC_PHI_LINE, "rline": POT3D_PC_R_LINE,
+            "lines": POT3D_PC_LINES}
 
 
 class pot3d_grid_t(ctypes.Structure):
@@ -276,7 +279,8 @@ class Plan:
 
     def set_opts(self, max_iters=0, use_x0=0, chunk=0, use_graphs=0, time_kernels=0,
                  inner_tol=0.0, max_outer=0, mixed_restart=0, verify=0, precond=0, history=0):
-        """pot3d_set_opts; precond: 0 / "jacobi" or 1 / "philine"."""
+        """pot3d_set_opts; precond: a POT3D_PC_* value or its name ("jacobi",
+        "philine", "rline", "lines")."""
         pc = PRECONDS.get(precond, precond)
         o = pot3d_opts_t(int(max_iters), int(use_x0), int(chunk), int(use_graphs), int(time_kernels),
                          float(inner_tol), int(max_outer), int(mixed_restart), int(verify),

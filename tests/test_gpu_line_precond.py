@@ -1,9 +1,18 @@
-"""GPU parity of the phi-line preconditioner (opts.precond =
-POT3D_PC_PHI_LINE: one cyclic tridiagonal solve per (r, theta) ring, the
-stronger line preconditioner of the kind Sec. 6 calls for) through the C ABI
-against the oracle's phi-line PCG, which solves its rings by a different
-algorithm (Sherman-Morrison around a Thomas solve; the GPU factors the ring
-into two first-order recurrences)."""
+"""GPU parity of the line preconditioners through the C ABI against the
+oracle's PCG with the same preconditioner (stronger preconditioners that
+still vectorise, the direction Sec. 6 names):
+- POT3D_PC_PHI_LINE ("philine"): one cyclic tridiagonal solve per (r, theta)
+  ring.  The oracle solves a ring by Sherman-Morrison around a Thomas solve;
+  the GPU factors it into two first-order recurrences.
+- POT3D_PC_R_LINE ("rline"): one tridiagonal solve per (theta, phi) column.
+  The oracle runs the Thomas algorithm per column with its divisions; the
+  GPU takes the factors l_i, d'_i of every theta row from a table and runs
+  the forward and backward recurrences on w = D z.
+- POT3D_PC_LINES ("lines"): M^-1 = T_r^-1 + T_phi^-1 - D^-1 (the phi-line
+  update forms D (T_phi^-1 - D^-1) r, the column kernel adds D T_r^-1 r).
+"""
+import os
+
 import numpy as np
 import pytest
 
@@ -44,7 +53,13 @@ GRIDS = [
     ((17, 35, 129), 1.02, "bip", "source"),
     ((5, 6, 3), 1.0, "bip", "source"),
     ((12, 17, 40), 1.03, "bip", "closed"),
+    # radial couplings dominate (thin inner cells): the radial-line regime
+    ((49, 15, 25), 1.08, "bip", "source"),
+    # fewer radial cells than the column kernel's prefetch depth (4)
+    ((3, 9, 40), 1.0, "bip", "source"),
+    ((33, 19, 45), 1.06, "bip", "closed"),
 ]
+KINDS = ["philine", "rline", "lines"]
 
 
 def make_br(kind, nt, np_):
@@ -53,15 +68,16 @@ def make_br(kind, nt, np_):
     return syn.bipole_br(nt, np_, seed=1709, n_bipoles=30)
 
 
+@pytest.mark.parametrize("pc", KINDS)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("shape,ratio,kind,outer", GRIDS)
-def test_phi_line_solve_parity(p3, oracle_mod, prec, shape, ratio, kind, outer):
+def test_line_solve_parity(p3, oracle_mod, pc, prec, shape, ratio, kind, outer):
     nr, nt, np_ = shape
     br = make_br(kind, nt, np_)
-    g = oracle_mod.Grid(*shape, ratio=ratio, outer=outer, precond="philine")
+    g = oracle_mod.Grid(*shape, ratio=ratio, outer=outer, precond=pc)
     ref, it_ref, st = g.solve(br, 1e-12)
     assert st == oracle_mod.OK
-    plan = p3.Plan(*shape, ratio=ratio, precision=prec, outer=outer, precond="philine")
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec, outer=outer, precond=pc)
     phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, it = plan.solve(dev(br), 1e-12, phi)
     x = host(phi)
@@ -76,20 +92,70 @@ def test_phi_line_solve_parity(p3, oracle_mod, prec, shape, ratio, kind, outer):
     plan.close()
 
 
-def test_phi_line_history_and_fewer_iterations(p3, oracle_mod):
-    """The residual history follows the oracle's phi-line history; the
-    same solution is reached in fewer iterations than with diagonal
-    scaling."""
-    shape, ratio = (17, 35, 129), 1.02
-    br = make_br("bip", 35, 129)
-    g = oracle_mod.Grid(*shape, ratio=ratio, precond="philine")
-    _, it_ref, _, h_ref = g.pcg(g.rhs(br), 1e-12, history=True)
-    plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond="philine", history=1)
+@pytest.mark.parametrize("pc", KINDS)
+def test_line_first_iterates(p3, oracle_mod, pc):
+    """The first PCG iterates against the oracle's: x_1 = alpha_0 M^-1 b
+    shows the preconditioner's application itself; later iterates follow
+    it within rounding (relative 1e-12: a few iterations of FP64 PCG that
+    add their sums in other orders)."""
+    shape, ratio = (49, 15, 25), 1.08
+    br = make_br("bip", 15, 25)
+    g = oracle_mod.Grid(*shape, ratio=ratio, precond=pc)
+    b = g.rhs(br)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for k in (1, 2, 5, 20):
+        x_ref, _, _ = g.pcg(b, 1e-300, maxit=k)
+        plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond=pc, max_iters=k)
+        rc, it = plan.solve(dev(br), 1e-300, phi, check=False)
+        assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == k
+        assert rel(host(phi), x_ref) <= 1e-12, (k, rel(host(phi), x_ref))
+        plan.close()
+
+
+# (preconditioner, grid, ratio): phi lines where phi couplings dominate (fine
+# phi rows near the poles), radial lines where thin inner cells make the
+# radial couplings dominate, both directions on each
+FEWER = [
+    ("philine", (17, 35, 129), 1.02),
+    ("lines", (17, 35, 129), 1.02),
+    ("rline", (49, 15, 25), 1.08),
+    ("lines", (49, 15, 25), 1.08),
+]
+
+
+@pytest.mark.parametrize("pc,shape,ratio", FEWER)
+def test_line_history_and_fewer_iterations(p3, oracle_mod, pc, shape, ratio):
+    """The residual history follows the oracle's history with the same
+    preconditioner; the same solution is reached in fewer iterations than
+    with diagonal scaling (oracle: 162 / 168 against 732 at 17 x 35 x 129,
+    123 / 109 against 1021 at 49 x 15 x 25).
+
+    History bar: 4 x the oracle's own spread under other thread counts
+    (other reduction orders; measured 3e-10 for phi lines and 3.1e-4 for
+    both directions at 17 x 35 x 129: the sum of two line inverses makes the
+    late iterations more sensitive), and at least 1e-6, the allowance for
+    the GPU's line solves, which are other algorithms than the oracle's
+    (recurrences against Thomas / Sherman-Morrison) and round differently."""
+    br = make_br("bip", shape[1], shape[2])
+    g = oracle_mod.Grid(*shape, ratio=ratio, precond=pc)
+    b = g.rhs(br)
+    n = os.cpu_count() or 1
+    oracle_mod.set_threads(n)
+    _, it_ref, _, h_ref = g.pcg(b, 1e-12, history=True)
+    spread = 0.0
+    for t in sorted({1, 2, 3} - {n}):
+        oracle_mod.set_threads(t)
+        _, _, _, h_t = g.pcg(b, 1e-12, history=True)
+        m = min(len(h_t), len(h_ref))
+        spread = max(spread, np.max(np.abs(h_t[:m] - h_ref[:m]) / h_ref[:m]))
+    oracle_mod.set_threads(n)
+    plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond=pc, history=1)
     phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, it = plan.solve(dev(br), 1e-12, phi)
     h = plan.history()
     m = min(len(h), len(h_ref))
-    assert np.max(np.abs(h[:m] - h_ref[:m]) / h_ref[:m]) <= 1e-6
+    dev_h = np.max(np.abs(h[:m] - h_ref[:m]) / h_ref[:m])
+    assert dev_h <= max(1e-6, 4.0 * spread), (dev_h, spread)
     pj = p3.Plan(*shape, ratio=ratio, precision="fp64")
     phj = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, itj = pj.solve(dev(br), 1e-12, phj)
@@ -99,21 +165,22 @@ def test_phi_line_history_and_fewer_iterations(p3, oracle_mod):
     pj.close()
 
 
+@pytest.mark.parametrize("pc", KINDS)
 @pytest.mark.parametrize("arith", ["fp64", "f32"])
-def test_phi_line_every_decomposition(p3, oracle_mod, arith):
+def test_line_every_decomposition(p3, oracle_mod, pc, arith):
     """Every matvec variant and update work-item size keeps parity with the
-    phi-line preconditioner (the ring solve runs inside the update kernel,
-    so its work items must hold whole rings)."""
+    line preconditioners (the ring solve runs inside the update kernel, so
+    its work items must hold whole rings; the matvec reads w in place of r)."""
     shape, ratio = (14, 37, 150), 1.03
     br = make_br("bip", 37, 150)
-    g = oracle_mod.Grid(*shape, ratio=ratio, precond="philine")
+    g = oracle_mod.Grid(*shape, ratio=ratio, precond=pc)
     ref, it_ref, _ = g.solve(br, 1e-12)
     b = g.rhs(br)
     prec = {"fp64": "fp64", "f32": "mixed"}[arith]
     phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
     for v in range(len(p3.variants(arith))):
         for chunks, rows in ((1, 16), (3, 150)):
-            plan = p3.Plan(*shape, ratio=ratio, precision=prec, precond="philine")
+            plan = p3.Plan(*shape, ratio=ratio, precision=prec, precond=pc)
             plan.set_decomposition(arith, v, chunks, rows)
             rc, it = plan.solve(dev(br), 1e-12 if prec == "fp64" else 1e-11, phi)
             x = host(phi)
@@ -124,10 +191,18 @@ def test_phi_line_every_decomposition(p3, oracle_mod, arith):
             plan.close()
 
 
-def test_phi_line_unsupported_paths(p3):
-    plan = p3.Plan(6, 7, 9, precision="df", precond="philine")
+@pytest.mark.parametrize("pc", KINDS)
+def test_line_unsupported_paths(p3, pc):
+    plan = p3.Plan(6, 7, 9, precision="df", precond=pc)
     phi = torch.zeros((6, 7, 9), dtype=torch.float64, device="cuda")
     br = torch.ones((7, 9), dtype=torch.float64, device="cuda")
     rc, _ = plan.solve(br, 1e-10, phi, check=False)
     assert rc == p3.POT3D_ERR_UNSUPPORTED
     plan.close()
+    # batches take diagonal scaling and phi lines only
+    if pc == "philine":
+        p3.Batch(1 << 26, max_slots=1, precond=pc).close()
+    else:
+        with pytest.raises(p3.Pot3dError) as e:
+            p3.Batch(1 << 26, max_slots=1, precond=pc)
+        assert e.value.code == p3.POT3D_ERR_UNSUPPORTED
