@@ -495,16 +495,16 @@ def run_gpu(args):
 
 def precond_record(pot3d, torch, dev, br_d, steps=2):
     """Time to solution of the same 151x301x601 solve to 1e-10 with diagonal
-    scaling (PC1, the paper's) and with the phi-line preconditioner, in FP64
-    and in the mixed path: PCG iterations, seconds per solve (CUDA events on
-    torch's stream, after one warm-up solve) and the FP64 residual of the
-    result."""
+    scaling (PC1, the paper's) and with the line preconditioners (phi lines,
+    radial lines, both directions), in FP64 and in the mixed path: PCG
+    iterations, seconds per solve (CUDA events on torch's stream, after one
+    warm-up solve) and the FP64 residual of the result."""
     out = {}
     stream = torch.cuda.current_stream(dev)
     phi = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
     for prec in ("fp64", "mixed"):
         out[prec] = {}
-        for pc in ("jacobi", "philine"):
+        for pc in ("jacobi", "philine", "rline", "lines"):
             plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=prec, precond=pc)
             plan.autotune(4 if prec == "mixed" else 0)
             plan.set_opts(precond=pc)
@@ -529,9 +529,11 @@ def precond_record(pot3d, torch, dev, br_d, steps=2):
                              "relres_fp64": st["relres_fp64"],
                              "iters_per_s": its[-1] / sec}
             plan.close()
-        j, l = out[prec]["jacobi"], out[prec]["philine"]
-        out[prec]["speedup_time_to_solution"] = j["s_per_solve"] / l["s_per_solve"]
-        out[prec]["iteration_ratio"] = j["iters"] / l["iters"]
+        j = out[prec]["jacobi"]
+        for pc in ("philine", "rline", "lines"):
+            l = out[prec][pc]
+            l["speedup_time_to_solution"] = j["s_per_solve"] / l["s_per_solve"]
+            l["iteration_ratio"] = j["iters"] / l["iters"]
     return out
 
 
@@ -755,7 +757,7 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine"],
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine", "rline", "lines"],
                     help="the preconditioner of --profile-case and --workload large-solve")
     ap.add_argument("--profile-field", action="store_true",
                     help="with --profile-case: also three field evaluations")

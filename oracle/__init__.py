@@ -11,10 +11,12 @@ field code, written step by step from the paper:
   average.
 - Sec. 2.2 (finite-difference stencil) and Eq. 4: the 7-point operator, in
   its symmetric volume-weighted form with the r^2 metric factors restored.
-- Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1); as the stronger
-  preconditioners Sec. 6 asks for, radial-line Jacobi (one tridiagonal solve
-  per (theta, phi) column) and phi-line Jacobi (one cyclic tridiagonal solve
-  per (r, theta) ring).
+- Sec. 2.3: PCG with point-Jacobi / diagonal scaling (PC1) and with PC2,
+  the non-overlapping domain decomposition with a zero-fill incomplete LU
+  factorisation (ILU(0), Saad Algorithm 10.4) of each subdomain's block;
+  as the stronger preconditioners Sec. 6 asks for, radial-line Jacobi (one
+  tridiagonal solve per (theta, phi) column) and phi-line Jacobi (one cyclic
+  tridiagonal solve per (r, theta) ring).
 
 The wrapper below only marshals numpy arrays into the C routines.
 """
@@ -70,6 +72,7 @@ def _load():
             lib.orc_csr.restype = ctypes.c_long
             lib.orc_set_outer.argtypes = [i]
             lib.orc_set_precond.argtypes = [i]
+            lib.orc_set_blocks.argtypes = [i, i, i]
             lib.orc_precond.argtypes = [i, i, i, _dp, _dp, _dp, _dp]
             lib.orc_balance_br.argtypes = [i, i, i, _dp, _dp, _dp, _dp]
             lib.orc_remove_mean.argtypes = [ctypes.c_long, _dp]
@@ -94,7 +97,7 @@ def get_threads() -> int:
 
 
 OUTER = {"source": 0, "closed": 1}
-PRECOND = {"jacobi": 0, "rline": 1, "philine": 2, "lines": 3}
+PRECOND = {"jacobi": 0, "rline": 1, "philine": 2, "lines": 3, "ilu": 4}
 
 
 class Grid:
@@ -105,14 +108,17 @@ class Grid:
     ``t_faces`` is given.  ``outer``: "source" (source surface, Phi = 0 at r1)
     or "closed" (closed wall, Br = 0 at r1), Sec. 2.1.  ``precond``: "jacobi"
     (diagonal scaling, PC1 of Sec. 2.3), "rline" (radial-line Jacobi) or
-    "philine" (phi-line Jacobi: one cyclic tridiagonal solve per ring) or
-    "lines" (both: M^-1 = T_r^-1 + T_phi^-1 - D^-1)."""
+    "philine" (phi-line Jacobi: one cyclic tridiagonal solve per ring),
+    "lines" (both: M^-1 = T_r^-1 + T_phi^-1 - D^-1) or "ilu" (PC2: ILU(0)
+    of every subdomain box of ``blocks`` = (cells in r, theta, phi; 0 = the
+    whole extent), couplings between boxes dropped)."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
-                 outer="source", precond="jacobi"):
+                 outer="source", precond="jacobi", blocks=(0, 4, 8)):
         self.nr, self.nt, self.np = int(nr), int(nt), int(np_)
         self.outer = outer
         self.precond = precond
+        self.blocks = tuple(int(b) for b in blocks)
         lib = _load()
         if r_faces is None:
             rf = np.empty(self.nr + 1)
@@ -152,6 +158,7 @@ class Grid:
     def _dims(self):
         _load().orc_set_outer(OUTER[self.outer])
         _load().orc_set_precond(PRECOND[self.precond])
+        _load().orc_set_blocks(*self.blocks)
         return self.nr, self.nt, self.np, _p(self.rf), _p(self.tf)
 
     # -- operator (Sec. 2.2, Eq. 4) --------------------------------------

@@ -72,7 +72,10 @@ typedef struct {
 
 static int g_threads = 0;
 static int g_outer_closed = 0; /* 0: source surface Phi = 0; 1: closed wall Br = 0 */
-static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi lines */
+static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi lines;
+                            3: both line directions; 4: subdomain ILU(0) (PC2) */
+/* PC2 subdomain box: cells in r, theta, phi (0 = the whole extent) */
+static int g_blk[3] = {0, 4, 8};
 
 /* Preconditioner of orc_pcg (line preconditioners are of the kind Sec. 6
  * asks for: stronger than diagonal scaling, yet every line independent):
@@ -89,10 +92,30 @@ static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi line
  *       both sides it is I + f(K_r) + f(K_phi), f(K) = K (I - K)^-1, where
  *       K = D^-1/2 C D^-1/2 holds one line direction's couplings C; the
  *       eigenvalues l of K lie in (-1, 1), so those of f(K), l / (1 - l),
- *       exceed -1/2, and the sum stays above 0. */
+ *       exceed -1/2, and the sum stays above 0;
+ *   4 = PC2 of Sec. 2.3: non-overlapping domain decomposition with a
+ *       zero-fill incomplete LU factorisation (ILU(0)) of each subdomain's
+ *       block of L.  The subdomains are boxes of g_blk cells (orc_set_blocks;
+ *       the last box of each direction holds the remainder); couplings
+ *       between boxes are dropped (block Jacobi over the subdomains), a box
+ *       that spans the whole phi ring keeps the periodic coupling inside
+ *       it.  Within a box the unknowns are numbered in C order (r slowest,
+ *       phi fastest).  For the 7-point pattern any lexicographic numbering
+ *       with every axis ascending orients each coupling the same way (the
+ *       cell with the larger r, theta or phi index comes later), so the
+ *       paper's r-fastest FORTRAN numbering gives the same factors. */
 int orc_set_precond(int kind) {
-  if (kind < 0 || kind > 3) return 3;
+  if (kind < 0 || kind > 4) return 3;
   g_precond = kind;
+  return 0;
+}
+
+/* Box of the PC2 subdomains: bi x bj x bk cells (0 = the whole extent). */
+int orc_set_blocks(int bi, int bj, int bk) {
+  if (bi < 0 || bj < 0 || bk < 0) return 3;
+  g_blk[0] = bi;
+  g_blk[1] = bj;
+  g_blk[2] = bk;
   return 0;
 }
 
@@ -371,8 +394,187 @@ static void precond_rline(const orc_op *op, const double *r, double *z) {
   }
 }
 
-static void precond_apply(const orc_op *op, const double *r, double *z) {
-  if (g_precond == 0) {
+/* ------------------------------------------------- PC2: subdomain ILU(0) */
+
+/* The block-diagonal matrix of the subdomain blocks of L in box order
+ * (box by box, C order inside a box), stored in CSR with sorted columns,
+ * factored in place by ILU(0): below the diagonal the multipliers of the
+ * unit lower factor, on and above it the upper factor. */
+typedef struct {
+  long n, nbox;
+  long *perm;   /* perm[m]: unknown index (C order of the grid) of box-order row m */
+  long *bstart; /* [nbox + 1]: first box-order row of each box */
+  long *rowptr; /* [n + 1] */
+  long *col;    /* box-order column indices */
+  double *val;
+  long *dpos;   /* position of each row's diagonal entry */
+} orc_ilu;
+
+static void ilu_free(orc_ilu *f) {
+  free(f->perm); free(f->bstart); free(f->rowptr); free(f->col); free(f->val); free(f->dpos);
+  memset(f, 0, sizeof(*f));
+}
+
+/* number of boxes of extent b (0: one box) along an axis of n cells */
+static int nboxes(int n, int b) { return (b <= 0 || b >= n) ? 1 : (n + b - 1) / b; }
+static int boxlen(int n, int b) { return (b <= 0 || b >= n) ? n : b; }
+
+/* Assemble the subdomain blocks of L and factor each by ILU(0), Saad,
+ * Iterative Methods for Sparse Linear Systems, Algorithm 10.4 (IKJ form):
+ *   for each row i, for each k < i with (i, k) in NZ(A), in column order:
+ *     a_ik := a_ik / a_kk;
+ *     for each j > k with (i, j) in NZ(A):  a_ij := a_ij - a_ik a_kj
+ * (a_kj taken as 0 where (k, j) is not in NZ(A): no fill).  Returns ORC_OK,
+ * ORC_BREAKDOWN when a pivot is not positive, ORC_BAD_ARG on allocation
+ * failure. */
+static int ilu_build(const orc_op *op, orc_ilu *f) {
+  memset(f, 0, sizeof(*f));
+  const int nr = op->nr, nt = op->nt, np = op->np;
+  const long n = (long)nr * nt * np, plane = (long)nt * np;
+  const int Li = boxlen(nr, g_blk[0]), Lj = boxlen(nt, g_blk[1]), Lk = boxlen(np, g_blk[2]);
+  const int Bi = nboxes(nr, g_blk[0]), Bj = nboxes(nt, g_blk[1]), Bk = nboxes(np, g_blk[2]);
+  f->n = n;
+  f->nbox = (long)Bi * Bj * Bk;
+  f->perm = malloc(sizeof(long) * n);
+  f->bstart = malloc(sizeof(long) * (f->nbox + 1));
+  f->rowptr = malloc(sizeof(long) * (n + 1));
+  f->col = malloc(sizeof(long) * 7 * n);
+  f->val = malloc(sizeof(double) * 7 * n);
+  f->dpos = malloc(sizeof(long) * n);
+  long *inv = malloc(sizeof(long) * n);
+  if (!f->perm || !f->bstart || !f->rowptr || !f->col || !f->val || !f->dpos || !inv) {
+    free(inv);
+    ilu_free(f);
+    return ORC_BAD_ARG;
+  }
+  /* box order: boxes in C order of their box indices, cells in C order */
+  long m = 0, b = 0;
+  for (int bi = 0; bi < Bi; bi++)
+    for (int bj = 0; bj < Bj; bj++)
+      for (int bk = 0; bk < Bk; bk++) {
+        f->bstart[b++] = m;
+        for (int i = bi * Li; i < nr && i < (bi + 1) * Li; i++)
+          for (int j = bj * Lj; j < nt && j < (bj + 1) * Lj; j++)
+            for (int k = bk * Lk; k < np && k < (bk + 1) * Lk; k++) {
+              const long c = (long)i * plane + (long)j * np + k;
+              f->perm[m] = c;
+              inv[c] = m;
+              m++;
+            }
+      }
+  f->bstart[f->nbox] = n;
+  /* rows: the couplings of L whose two cells lie in the same box */
+  long nnz = 0;
+  f->rowptr[0] = 0;
+  for (long row = 0; row < n; row++) {
+    const long c = f->perm[row];
+    const int i = (int)(c / plane), j = (int)((c / np) % nt), k = (int)(c % np);
+    const long box = ((long)(i / Li) * Bj + j / Lj) * Bk + k / Lk;
+    long cols[8];
+    double vals[8];
+    int cnt = 0;
+    cols[cnt] = row; vals[cnt] = op->diag[i * nt + j]; cnt++;
+    /* neighbour (ii, jj, kk) with coupling -coef, kept if in the same box */
+#define ORC_NB(ii, jj, kk, coef)                                                              \
+  do {                                                                                       \
+    const long nbbox = ((long)((ii) / Li) * Bj + (jj) / Lj) * Bk + (kk) / Lk;               \
+    if (nbbox == box) {                                                                      \
+      cols[cnt] = inv[(long)(ii) * plane + (long)(jj) * np + (kk)];                          \
+      vals[cnt] = -(coef);                                                                   \
+      cnt++;                                                                                 \
+    }                                                                                        \
+  } while (0)
+    if (i < nr - 1) ORC_NB(i + 1, j, k, op->cr[i * nt + j]);
+    if (i > 0) ORC_NB(i - 1, j, k, op->cr[(i - 1) * nt + j]);
+    if (j < nt - 1) ORC_NB(i, j + 1, k, op->ct[i * (nt - 1) + j]);
+    if (j > 0) ORC_NB(i, j - 1, k, op->ct[i * (nt - 1) + j - 1]);
+    const int kp = (k + 1) % np, km = (k + np - 1) % np;
+    if (kp == km) {
+      /* np == 2: both phi faces couple to the one other cell */
+      ORC_NB(i, j, kp, 2.0 * op->cp[i * nt + j]);
+    } else {
+      ORC_NB(i, j, kp, op->cp[i * nt + j]);
+      ORC_NB(i, j, km, op->cp[i * nt + j]);
+    }
+#undef ORC_NB
+    for (int a = 1; a < cnt; a++) {
+      long cc = cols[a]; double vv = vals[a]; int q = a - 1;
+      while (q >= 0 && cols[q] > cc) { cols[q + 1] = cols[q]; vals[q + 1] = vals[q]; q--; }
+      cols[q + 1] = cc; vals[q + 1] = vv;
+    }
+    for (int a = 0; a < cnt; a++) {
+      if (cols[a] == row) f->dpos[row] = nnz;
+      f->col[nnz] = cols[a];
+      f->val[nnz] = vals[a];
+      nnz++;
+    }
+    f->rowptr[row + 1] = nnz;
+  }
+  free(inv);
+  /* ILU(0), box by box (no coupling crosses a box) */
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+  for (long bx = 0; bx < f->nbox; bx++) {
+    for (long i = f->bstart[bx]; i < f->bstart[bx + 1]; i++) {
+      for (long e = f->rowptr[i]; e < f->rowptr[i + 1] && f->col[e] < i; e++) {
+        const long k = f->col[e];
+        const double piv = f->val[f->dpos[k]];
+        if (!(piv > 0.0)) { bad = 1; break; }
+        f->val[e] /= piv;
+        for (long g = e + 1; g < f->rowptr[i + 1]; g++) {
+          const long jcol = f->col[g];
+          for (long h = f->rowptr[k]; h < f->rowptr[k + 1]; h++) {
+            if (f->col[h] == jcol) { f->val[g] -= f->val[e] * f->val[h]; break; }
+          }
+        }
+      }
+      if (!(f->val[f->dpos[i]] > 0.0)) bad = 1;
+    }
+  }
+  if (bad) {
+    ilu_free(f);
+    return ORC_BREAKDOWN;
+  }
+  return ORC_OK;
+}
+
+/* z = (LU)^-1 r box by box: forward substitution with the unit lower
+ * factor, then back substitution with the upper factor. */
+static void precond_ilu(const orc_ilu *f, const double *r, double *z) {
+#pragma omp parallel
+  {
+    long cap = 0;
+    double *y = NULL;
+#pragma omp for schedule(dynamic, 16)
+    for (long bx = 0; bx < f->nbox; bx++) {
+      const long b0 = f->bstart[bx], b1 = f->bstart[bx + 1];
+      if (b1 - b0 > cap) {
+        free(y);
+        cap = b1 - b0;
+        y = malloc(sizeof(double) * cap);
+      }
+      /* L y = r:  y_i = r_i - sum_{k<i} l_ik y_k */
+      for (long i = b0; i < b1; i++) {
+        double s = r[f->perm[i]];
+        for (long e = f->rowptr[i]; e < f->dpos[i]; e++) s -= f->val[e] * y[f->col[e] - b0];
+        y[i - b0] = s;
+      }
+      /* U z = y:  z_i = (y_i - sum_{j>i} u_ij z_j) / u_ii, stored in y */
+      for (long i = b1 - 1; i >= b0; i--) {
+        double s = y[i - b0];
+        for (long e = f->dpos[i] + 1; e < f->rowptr[i + 1]; e++) s -= f->val[e] * y[f->col[e] - b0];
+        y[i - b0] = s / f->val[f->dpos[i]];
+      }
+      for (long i = b0; i < b1; i++) z[f->perm[i]] = y[i - b0];
+    }
+    free(y);
+  }
+}
+
+static void precond_apply(const orc_op *op, const orc_ilu *ilu, const double *r, double *z) {
+  if (g_precond == 4) {
+    precond_ilu(ilu, r, z);
+  } else if (g_precond == 0) {
     precond_jacobi(op, r, z);
   } else if (g_precond == 1) {
     precond_rline(op, r, z);
@@ -438,7 +640,14 @@ int orc_precond(int nr, int nt, int np, const double *rf, const double *tf, cons
   orc_op op;
   int st = op_build(&op, nr, nt, np, rf, tf);
   if (st) return st;
-  precond_apply(&op, r, z);
+  orc_ilu ilu;
+  memset(&ilu, 0, sizeof(ilu));
+  if (g_precond == 4 && (st = ilu_build(&op, &ilu)) != ORC_OK) {
+    op_free(&op);
+    return st;
+  }
+  precond_apply(&op, &ilu, r, z);
+  ilu_free(&ilu);
   op_free(&op);
   return ORC_OK;
 }
@@ -522,7 +731,9 @@ int orc_rhs(int nr, int nt, int np, const double *rf, const double *tf, const do
 
 /* Textbook preconditioned conjugate gradient (Saad, Iterative Methods,
  * Algorithm 9.1) with the preconditioner of orc_set_precond: point Jacobi
- * (diagonal scaling, PC1 of Sec. 2.3) by default, or radial-line Jacobi.  x holds the initial guess when x0_given != 0, else it is
+ * (diagonal scaling, PC1 of Sec. 2.3) by default, a line preconditioner, or
+ * the subdomain ILU(0) (PC2 of Sec. 2.3, factored once per call).  x holds
+ * the initial guess when x0_given != 0, else it is
  * zeroed.  Stops after iteration k when ||r_k||_2 / ||b||_2 <= tol.
  * relres (optional, length maxit+1) receives ||r_k||/||b|| for k = 0..iters.
  * Returns ORC_OK, ORC_NOT_CONVERGED (iters == maxit, x = last iterate) or
@@ -552,8 +763,16 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
     for (long c = 0; c < n; c++) { x[c] = 0.0; r[c] = b[c]; }
   }
   const double bnorm = sqrt(dot(n, b, b));
+  /* PC2: the subdomain ILU(0) factors, once per solve */
+  orc_ilu ilu;
+  memset(&ilu, 0, sizeof(ilu));
+  if (g_precond == 4 && (st = ilu_build(&op, &ilu)) != ORC_OK) {
+    free(r); free(z); free(p); free(q);
+    op_free(&op);
+    return st;
+  }
   /* z_0 = M^-1 r_0 */
-  precond_apply(&op, r, z);
+  precond_apply(&op, &ilu, r, z);
   /* p_0 = z_0 */
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < n; c++) p[c] = z[c];
@@ -582,7 +801,7 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
     if (relres) relres[k] = rn / bnorm;
     if (rn / bnorm <= tol) { status = ORC_OK; break; }
     /* z = M^-1 r */
-    precond_apply(&op, r, z);
+    precond_apply(&op, &ilu, r, z);
     /* beta = (r_new . z_new) / (r_old . z_old) */
     double rho_new = dot(n, r, z);
     double beta = rho_new / rho;
@@ -593,6 +812,7 @@ int orc_pcg(int nr, int nt, int np, const double *rf, const double *tf, const do
   }
   *iters = k;
   free(r); free(z); free(p); free(q);
+  ilu_free(&ilu);
   op_free(&op);
   return status;
 }
