@@ -495,8 +495,9 @@ def run_gpu(args):
 
 def precond_record(pot3d, torch, dev, br_d, steps=2):
     """Time to solution of the same 151x301x601 solve to 1e-10 with diagonal
-    scaling (PC1, the paper's) and with the line preconditioners (phi lines,
-    radial lines, both directions), in FP64 and in the mixed path: PCG
+    scaling (PC1, the paper's), with the line preconditioners (phi lines,
+    radial lines, both directions) and with PC2 (the paper's subdomain
+    ILU(0)), in FP64 and in the mixed path: PCG
     iterations, seconds per solve (CUDA events on torch's stream, after one
     warm-up solve) and the FP64 residual of the result."""
     out = {}
@@ -504,7 +505,7 @@ def precond_record(pot3d, torch, dev, br_d, steps=2):
     phi = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
     for prec in ("fp64", "mixed"):
         out[prec] = {}
-        for pc in ("jacobi", "philine", "rline", "lines"):
+        for pc in ("jacobi", "philine", "rline", "lines", "ilu"):
             plan = pot3d.Plan(*SHAPE, ratio=RATIO, precision=prec, precond=pc)
             plan.autotune(4 if prec == "mixed" else 0)
             plan.set_opts(precond=pc)
@@ -530,7 +531,7 @@ def precond_record(pot3d, torch, dev, br_d, steps=2):
                              "iters_per_s": its[-1] / sec}
             plan.close()
         j = out[prec]["jacobi"]
-        for pc in ("philine", "rline", "lines"):
+        for pc in ("philine", "rline", "lines", "ilu"):
             l = out[prec][pc]
             l["speedup_time_to_solution"] = j["s_per_solve"] / l["s_per_solve"]
             l["iteration_ratio"] = j["iters"] / l["iters"]
@@ -757,7 +758,7 @@ def main():
     ap.add_argument("--profile-case", choices=["fp64", "df", "mixed"], default=None,
                     help="run a short capped solve for ncu and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine", "rline", "lines"],
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "philine", "rline", "lines", "ilu"],
                     help="the preconditioner of --profile-case and --workload large-solve")
     ap.add_argument("--profile-field", action="store_true",
                     help="with --profile-case: also three field evaluations")

@@ -81,6 +81,18 @@ extern "C" {
                                f(K) = K (I - K)^-1 with K one direction's scaled
                                couplings (eigenvalues in (-1, 1)), and each f(K) has
                                eigenvalues above -1/2.  FP64 and MIXED plans          */
+#define POT3D_PC_ILU 4      /* PC2 of Sec. 2.3: non-overlapping domain decomposition
+                               with a zero-fill incomplete LU factorisation (ILU(0))
+                               of every subdomain's block of L, couplings between
+                               subdomains dropped.  The subdomains are boxes of every
+                               r cell x 1 theta row x 32 phi columns (the last box of
+                               a row takes the remainder; a box never closes the phi
+                               ring, so np must exceed 32, else the solve returns
+                               POT3D_ERR_UNSUPPORTED).  For the 7-point pattern
+                               ILU(0) keeps L's couplings and changes only the
+                               diagonal, so M = (P + E) P^-1 (P + E^T), E the strict
+                               lower part of the box block and P the pivots.  FP64
+                               and MIXED plans                                        */
 
 /* ---- boundary conditions (Sec. 2.1) ---------------------------------- */
 #define POT3D_OUTER_SOURCE_SURFACE 0 /* Phi = 0 at r = r1                              */
@@ -140,8 +152,8 @@ typedef struct {
                          report the FP64 residual and the restarts (outer_iters).
                          MIXED always stops on the FP64 residual.                */
   int precond;        /* POT3D_PC_*: the preconditioner.  The line preconditioners
-                         run with FP64 or MIXED plans (a FP64_DF solve returns
-                         POT3D_ERR_UNSUPPORTED); batches take POT3D_PC_JACOBI and
+                         and PC2 run with FP64 or MIXED plans (a FP64_DF solve
+                         returns POT3D_ERR_UNSUPPORTED); batches take POT3D_PC_JACOBI and
                          POT3D_PC_PHI_LINE (pot3d_batch_set_opts returns
                          POT3D_ERR_UNSUPPORTED for the others)                  */
   int history;        /* FP64 and FP64_DF: 1 = record the recurrence residual

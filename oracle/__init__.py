@@ -114,7 +114,7 @@ class Grid:
     whole extent), couplings between boxes dropped)."""
 
     def __init__(self, nr, nt, np_, r0=1.0, r1=2.5, ratio=1.0, r_faces=None, t_faces=None,
-                 outer="source", precond="jacobi", blocks=(0, 4, 8)):
+                 outer="source", precond="jacobi", blocks=(0, 1, 32)):
         self.nr, self.nt, self.np = int(nr), int(nt), int(np_)
         self.outer = outer
         self.precond = precond

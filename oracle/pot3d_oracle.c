@@ -75,7 +75,7 @@ static int g_outer_closed = 0; /* 0: source surface Phi = 0; 1: closed wall Br =
 static int g_precond = 0; /* 0: point Jacobi (PC1); 1: radial lines; 2: phi lines;
                             3: both line directions; 4: subdomain ILU(0) (PC2) */
 /* PC2 subdomain box: cells in r, theta, phi (0 = the whole extent) */
-static int g_blk[3] = {0, 4, 8};
+static int g_blk[3] = {0, 1, 32};
 
 /* Preconditioner of orc_pcg (line preconditioners are of the kind Sec. 6
  * asks for: stronger than diagonal scaling, yet every line independent):

@@ -448,9 +448,9 @@ int pot3d_batch_set_opts(pot3d_batch_t *batch, const pot3d_opts_t *o) {
   if (!batch || !o || o->inner_tol < 0 || !(o->inner_tol < 1.0) || o->max_outer < 0 ||
       o->max_iters < 0)
     return fail(POT3D_ERR_INVALID_ARG);
-  if (o->precond < 0 || o->precond > 3) return fail(POT3D_ERR_INVALID_ARG);
-  // the radial-line kernel works on one problem per launch
-  if (o->precond == POT3D_PC_R_LINE || o->precond == POT3D_PC_LINES)
+  if (o->precond < 0 || o->precond > 4) return fail(POT3D_ERR_INVALID_ARG);
+  // the radial-line and subdomain-ILU(0) kernels work on one problem per launch
+  if (o->precond == POT3D_PC_R_LINE || o->precond == POT3D_PC_LINES || o->precond == POT3D_PC_ILU)
     return fail(POT3D_ERR_UNSUPPORTED);
   Batch *B = reinterpret_cast<Batch *>(batch);
   const bool line = o->precond == POT3D_PC_PHI_LINE;

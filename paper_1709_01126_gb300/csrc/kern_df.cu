@@ -10,7 +10,7 @@ const MvVariant *mv_variants_df(int *count) {
   return v;
 }
 
-KLaunch update_launcher_df() { return &up_launch<PDF, kUpdThreadsDF, kUpdSegBytes, kUpdStagesDF>; }
-int update_occupancy_df() { return up_occupancy<PDF, kUpdThreadsDF, kUpdSegBytes, kUpdStagesDF>(); }
+KLaunch update_launcher_df() { return &ur_launch<PDF, kUpdRsThreads, kUpdRsVecs>; }
+int update_occupancy_df() { return ur_occupancy<PDF, kUpdRsThreads, kUpdRsVecs>(); }
 
 } // namespace pot3d

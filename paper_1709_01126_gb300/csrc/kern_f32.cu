@@ -11,14 +11,15 @@ const MvVariant *mv_variants_f32(int *count) {
   return v;
 }
 
-KLaunch update_launcher_f32() { return &up_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>; }
+KLaunch update_launcher_f32() { return &ur_launch<PF32, kUpdRsThreads, kUpdRsVecs>; }
 KLineLaunch update_line_launcher_f32() {
   return &up_line_launch<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>;
 }
 KRLaunch rline_launcher_f32(bool add) {
   return add ? &rl_launch<PF32, true> : &rl_launch<PF32, false>;
 }
-int update_occupancy_f32() { return up_occupancy<PF32, kUpdThreadsF32, kUpdSegBytes, kUpdStagesF32>(); }
+KILaunch ilu_launcher_f32() { return &il_launch<PF32>; }
+int update_occupancy_f32() { return ur_occupancy<PF32, kUpdRsThreads, kUpdRsVecs>(); }
 
 // Tables of all arithmetics (indices AR_F64 = 0, AR_DF = 1, AR_F32 = 2).
 const MvVariant *mv_variants_f64(int *count);
@@ -51,6 +52,13 @@ KRLaunch rline_launcher_f64(bool add);
 KRLaunch rline_launcher(int ai, bool add) {
   if (ai == 0) return rline_launcher_f64(add);
   if (ai == 2) return rline_launcher_f32(add);
+  return nullptr;
+}
+
+KILaunch ilu_launcher_f64();
+KILaunch ilu_launcher(int ai) {
+  if (ai == 0) return ilu_launcher_f64();
+  if (ai == 2) return ilu_launcher_f32();
   return nullptr;
 }
 

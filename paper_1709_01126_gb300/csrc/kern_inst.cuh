@@ -67,6 +67,13 @@ void up_launch(const ProbDev *probs, const int2 *work, const int *nwork, int gri
   k_update<A, NT, SEGB, STG><<<grid, NT, LY::BYTES, s>>>(probs, work, nwork, nullptr);
 }
 
+// Update of diagonal scaling with register-staged rows (k_update_rs).
+template <class A, int NT, int F>
+void ur_launch(const ProbDev *probs, const int2 *work, const int *nwork, int grid,
+               cudaStream_t s) {
+  k_update_rs<A, NT, F><<<grid, NT, 0, s>>>(probs, work, nwork);
+}
+
 // Phi-line update: the stage layout plus one ring buffer of `pitch` values
 // per warp.  Returns 0, or -1 when the shared memory would exceed what a
 // block may use (the ring is too long for this configuration).
@@ -95,7 +102,37 @@ void rl_launch(const ProbDev *probs, int grid, double *setup_out, cudaStream_t s
   k_rline<A, kRLineThreads, ADD><<<grid, kRLineThreads, 0, s>>>(probs, setup_out);
 }
 
-// resident blocks of the update kernel per SM (0 if the query fails)
+// PC2 kernel: kIluThreads threads, IluLayout bytes per warp.
+template <class A>
+int il_launch(const ProbDev *probs, int grid, int nr, double *setup_out, cudaStream_t s) {
+  const size_t bytes = (size_t)(kIluThreads / 32) * IluLayout<A>::warp_bytes(nr);
+  static size_t set_to = 0;
+  if (bytes > set_to) {
+    if (bytes > 227 * 1024 ||
+        cudaFuncSetAttribute(k_ilu<A, kIluThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    set_to = bytes;
+  }
+  k_ilu<A, kIluThreads><<<grid, kIluThreads, bytes, s>>>(probs, setup_out);
+  return 0;
+}
+
+// resident blocks of the diagonal-scaling update per SM (0 if the query fails)
+template <class A, int NT, int F>
+int ur_occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update_rs<A, NT, F>, NT, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// resident blocks of the bulk-copy update kernel per SM (0 if the query fails)
 template <class A, int NT, int SEGB, int STG>
 int up_occupancy() {
   using LY = UpLayout<NT, SEGB, STG>;

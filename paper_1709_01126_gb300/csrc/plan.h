@@ -29,6 +29,9 @@ struct ArithData {
   void *rcoef = nullptr; // radial-line table [4][nr][ntp] (see ensure_rline)
   double *part_c = nullptr; // [2 * tiles_c] radial-line partials
   int tiles_c = 0;
+  void *icoef = nullptr;    // PC2 table (see ensure_ilu)
+  double *part_i = nullptr; // [2 * tiles_i] PC2 partials
+  int tiles_i = 0;
   int graph_pc = 0; // the preconditioner the captured graph launches (POT3D_PC_*)
   ProbDev *d_prob = nullptr;
   SolveState *d_state = nullptr;
@@ -83,6 +86,7 @@ struct Plan {
   bool freeze_poll = false; // testing hook: the host re-reads a stale state snapshot
   bool line = false;         // the solve in progress runs the phi-line update
   bool rline = false;        // the solve in progress runs the radial-line kernel
+  bool ilu = false;          // the solve in progress runs the PC2 kernel
   double *d_hist = nullptr;  // residual history of the last PCG run (opts.history)
   int hist_alloc = 0, hist_n = 0;
 };
@@ -99,6 +103,10 @@ int ensure_line(Plan *P, int ai);
 int ensure_rline(Plan *P, int ai);
 // radial-line blocks of a plan (8 warps of 32 phi columns of one theta row)
 int rline_tiles(const Plan *P);
+// PC2 table and partials of arithmetic ai (AR_F64 or AR_F32), built on first use
+int ensure_ilu(Plan *P, int ai);
+// PC2 blocks of a plan (kIluThreads / 32 boxes of nr x 1 x 32 cells each)
+int ilu_tiles(const Plan *P);
 size_t workspace_bytes(const Plan *P);
 int ensure_workspace(Plan *P);
 void *ws_vec(const Plan *P, int v, size_t es);

@@ -331,6 +331,71 @@ int ensure_rline(Plan *P, int ai) {
   return rc;
 }
 
+// PC2 (subdomain ILU(0), k_ilu): boxes of nr x 1 x 32 cells.  Table, in
+// the arithmetic's coefficient type: [4][nr][ntp] c^r_{i-1/2}, c^r_{i+1/2},
+// D and c^ph per (i, j) (zero where the face is a boundary face), then the
+// pivot inverses skewed for the wavefront, [nt][nr + 31][32] with entry
+// (j, t, kk) = 1 / p(t - kk, j, kk) (0 outside 0 <= t - kk < nr), where
+//     p(i, j, kk) = D_ij - [i > 0] (c^r_{i-1/2,j})^2 / p(i-1, j, kk)
+//                        - [kk > 0] (c^ph_ij)^2 / p(i, j, kk-1)
+// (ILU(0) of the 7-point pattern changes only the diagonal; a box's cells
+// k0 + kk have the pivots of column kk whatever the box's width).
+int ilu_tiles(const Plan *P) {
+  const long units = (long)P->nt * ((P->np + 31) / 32);
+  return (int)((units + kIluThreads / 32 - 1) / (kIluThreads / 32));
+}
+
+int ensure_ilu(Plan *P, int ai) {
+  ArithData &A = P->ar[ai];
+  const int tiles = ilu_tiles(P);
+  if (A.tiles_i < tiles) {
+    cudaFree(A.part_i);
+    A.part_i = nullptr;
+    A.tiles_i = 0;
+    if (cudaMalloc(&A.part_i, sizeof(double) * 2 * tiles) != cudaSuccess) {
+      cudaGetLastError();
+      return POT3D_ERR_OOM;
+    }
+    A.tiles_i = tiles;
+  }
+  if (A.icoef) return POT3D_OK;
+  const int nr = P->nr, nt = P->nt, ntp = P->ntp, T = nr + 31;
+  const size_t R = P->R, RP = (size_t)nr * ntp;
+  std::vector<double> t(4 * RP + (size_t)nt * T * 32, 0.0);
+  std::vector<double> piv((size_t)nr * 32);
+  for (int j = 0; j < nt; j++) {
+    for (int i = 0; i < nr; i++) {
+      const size_t row = (size_t)i * nt + j, o = (size_t)i * ntp + j;
+      t[o] = P->c64h[C64_RM * R + row];
+      t[RP + o] = P->c64h[C64_RP * R + row];
+      t[2 * RP + o] = P->c64h[C64_D * R + row];
+      t[3 * RP + o] = P->c64h[C64_PH * R + row];
+    }
+    for (int i = 0; i < nr; i++) {
+      const size_t row = (size_t)i * nt + j;
+      const double D = P->c64h[C64_D * R + row], crm = P->c64h[C64_RM * R + row],
+                   cph = P->c64h[C64_PH * R + row];
+      for (int kk = 0; kk < 32; kk++) {
+        double p = D;
+        if (i > 0) p -= crm * crm / piv[(size_t)(i - 1) * 32 + kk];
+        if (kk > 0) p -= cph * cph / piv[(size_t)i * 32 + kk - 1];
+        if (!(p > 0.0)) return POT3D_ERR_BREAKDOWN;
+        piv[(size_t)i * 32 + kk] = p;
+      }
+    }
+    double *sk = t.data() + 4 * RP + (size_t)j * T * 32;
+    for (int tt = 0; tt < T; tt++)
+      for (int kk = 0; kk < 32; kk++) {
+        const int i = tt - kk;
+        if (i >= 0 && i < nr) sk[(size_t)tt * 32 + kk] = 1.0 / piv[(size_t)i * 32 + kk];
+      }
+  }
+  if (ai == AR_F64) return upload((double **)&A.icoef, t);
+  std::vector<float> h(t.size());
+  for (size_t u = 0; u < t.size(); u++) h[u] = (float)t[u];
+  return upload((float **)&A.icoef, h);
+}
+
 // ----------------------------------------------------------- workspace
 // Vectors: x~, r, p~0, p~1, q and, with a line preconditioner, w in
 // the iteration's arithmetic; x64, r64 in FP64 for refinement.
@@ -473,7 +538,7 @@ int pot3d_set_stream(pot3d_plan_t *plan, void *s) {
 int pot3d_set_opts(pot3d_plan_t *plan, const pot3d_opts_t *o) {
   if (!plan || !o) return fail(POT3D_ERR_INVALID_ARG);
   if (o->max_iters < 0 || o->chunk < 0 || o->inner_tol < 0 || !(o->inner_tol < 1.0) ||
-      o->max_outer < 0 || o->verify < 0 || o->verify > 1 || o->precond < 0 || o->precond > 3 ||
+      o->max_outer < 0 || o->verify < 0 || o->verify > 1 || o->precond < 0 || o->precond > 4 ||
       o->history < 0 || o->history > 1)
     return fail(POT3D_ERR_INVALID_ARG);
   Plan *P = reinterpret_cast<Plan *>(plan);

@@ -77,6 +77,8 @@ void plan_free(Plan *P) {
     cudaFree(A.part_c);
     cudaFree(A.lcoef);
     cudaFree(A.rcoef);
+    cudaFree(A.icoef);
+    cudaFree(A.part_i);
     cudaFree(A.d_tma);
     cudaFree(A.d_work_a);
     cudaFree(A.d_work_b);
@@ -194,11 +196,17 @@ static void launch_matvec(Plan *P, int ai) {
 // The update step of an iteration per preconditioner: PC1 and phi lines run
 // the update kernel; radial lines the column kernel alone (it is the whole
 // update); both directions the phi-line update (forming D (T_phi^-1 - D^-1) r)
-// and then the column kernel, which adds D T_r^-1 r and closes the iteration.
+// and then the column kernel, which adds D T_r^-1 r and closes the iteration;
+// PC2 the subdomain ILU(0) kernel alone (it is the whole update too).
 static int update_launches(const Plan *P) { return (P->line && P->rline) ? 2 : 1; }
 
 static void launch_update(Plan *P, int ai) {
   ArithData &D = P->ar[ai];
+  if (P->ilu) {
+    // the shared memory fits: checked by line_setup before the solve
+    ilu_launcher(ai)(D.d_prob, D.tiles_i, P->nr, nullptr, P->stream);
+    return;
+  }
   if (P->line) {
     // the shared memory fits: checked by line_setup before the solve
     update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, nullptr,
@@ -219,6 +227,12 @@ static int select_precond(Plan *P, int ai) {
   const int pc = P->opts.precond;
   P->line = pc == POT3D_PC_PHI_LINE || pc == POT3D_PC_LINES;
   P->rline = pc == POT3D_PC_R_LINE || pc == POT3D_PC_LINES;
+  P->ilu = pc == POT3D_PC_ILU;
+  if (P->ilu) {
+    // a box must not close the phi ring (np > 32)
+    if (!ilu_launcher(ai) || P->np <= 32) return POT3D_ERR_UNSUPPORTED;
+    TRY(ensure_ilu(P, ai));
+  }
   if (P->line) {
     if (!update_line_launcher(ai)) return POT3D_ERR_UNSUPPORTED;
     TRY(ensure_line(P, ai));
@@ -235,6 +249,11 @@ static int select_precond(Plan *P, int ai) {
 // w = D M^-1 r for the first matvec and ||r||^2, r.M^-1 r to sums[0..1].
 static int line_setup(Plan *P, int ai, double *sums) {
   ArithData &D = P->ar[ai];
+  if (P->ilu) {
+    if (ilu_launcher(ai)(D.d_prob, D.tiles_i, P->nr, sums, P->stream) != 0)
+      return POT3D_ERR_UNSUPPORTED; // the warps' rings do not fit in shared memory
+    P->stats.launches += 1;
+  }
   if (P->line) {
     if (update_line_launcher(ai)(D.d_prob, D.d_work_b, D.d_nwork + 1, D.tiles_b, P->pitch, sums,
                                  P->stream) != 0)
@@ -362,7 +381,7 @@ static int iterate(Plan *P, int ai, int iter0 = 0) {
     // while chunk N+1 runs, so the GPU does not idle on the round trip.  A
     // chunk queued after the solve stopped does nothing (its kernels see the
     // status and exit).
-    const int pc_key = (P->line ? 1 : 0) | (P->rline ? 2 : 0);
+    const int pc_key = (P->line ? 1 : 0) | (P->rline ? 2 : 0) | (P->ilu ? 4 : 0);
     if (graphs && (!D.graph || D.graph_chunk != chunk || D.graph_pc != pc_key)) {
       if (D.graph) cudaGraphExecDestroy(D.graph);
       D.graph = nullptr;
@@ -494,9 +513,10 @@ static void fill_prob(Plan *P, int ai, void *x, void *r, void *p0, void *p1, voi
   h.w = w;
   h.lcoef = P->line ? D.lcoef : nullptr;
   h.rcoef = P->rline ? D.rcoef : nullptr;
-  h.part_c = D.part_c;
-  h.tiles_c = D.tiles_c;
+  h.part_c = P->ilu ? D.part_i : D.part_c;
+  h.tiles_c = P->ilu ? D.tiles_i : D.tiles_c;
   h.lines = (P->line && P->rline) ? 1 : 0;
+  h.icoef = P->ilu ? D.icoef : nullptr;
 }
 
 static int status_code(int st) {
@@ -586,7 +606,7 @@ static int solve_pcg(Plan *P, int ai, const double *br, double tol, double *phi,
   const size_t es = sizeof(typename A::st);
   void *x = ws_vec(P, 0, es), *r = ws_vec(P, 1, es), *p0 = ws_vec(P, 2, es),
        *p1 = ws_vec(P, 3, es), *q = ws_vec(P, 4, es);
-  void *w = (P->line || P->rline) ? ws_vec(P, 5, es) : nullptr;
+  void *w = (P->line || P->rline || P->ilu) ? ws_vec(P, 5, es) : nullptr;
   ArithData &D = P->ar[ai];
   fill_prob<A>(P, ai, x, r, p0, p1, q, w);
   TRY(build_tma(P, ai));
@@ -691,7 +711,7 @@ static int solve_mixed(Plan *P, const double *br, double tol, double *phi, int *
   ArithData &D = P->ar[AR_F32];
   void *x = ws_vec(P, 0, 4), *r = ws_vec(P, 1, 4), *p0 = ws_vec(P, 2, 4), *p1 = ws_vec(P, 3, 4),
        *q = ws_vec(P, 4, 4);
-  void *w = (P->line || P->rline) ? ws_vec(P, 5, 4) : nullptr;
+  void *w = (P->line || P->rline || P->ilu) ? ws_vec(P, 5, 4) : nullptr;
   double *x64 = ws_x64(P), *r64 = ws_r64(P);
   fill_prob<PF32>(P, AR_F32, x, r, p0, p1, q, w);
   TRY(build_tma(P, AR_F32));
@@ -1033,6 +1053,7 @@ int tune_arith(Plan *P, int ai, TuneVal *best) {
   TRY(ensure_workspace(P));
   P->line = false; // the tuner times the diagonal-scaling kernels
   P->rline = false;
+  P->ilu = false;
   ArithData &D = P->ar[ai];
   const size_t es = sizeof(typename A::st);
   cudaStream_t s = P->stream;

@@ -39,8 +39,9 @@ POT3D_PC_JACOBI = 0
 POT3D_PC_PHI_LINE = 1
 POT3D_PC_R_LINE = 2
 POT3D_PC_LINES = 3
+POT3D_PC_ILU = 4
 PRECONDS = {"jacobi": POT3D_PC_JACOBI, "philine": POT3D_PC_PHI_LINE, "rline": POT3D_PC_R_LINE,
-            "lines": POT3D_PC_LINES}
+            "lines": POT3D_PC_LINES, "ilu": POT3D_PC_ILU}
 
 
 class pot3d_grid_t(ctypes.Structure):

@@ -1,0 +1,187 @@
+"""GPU parity of PC2 (Sec. 2.3: non-overlapping domain decomposition with
+ILU(0) of every subdomain block) through the C ABI, against the oracle's
+PCG with the same subdomains (boxes of every r cell x 1 theta row x 32 phi
+columns, blocks=(0, 1, 32)).  The oracle factors each box's CSR block by
+Saad's ILU(0) and substitutes row by row; the GPU builds the pivots from the
+7-point recurrence and runs the substitutions as a wavefront across a warp.
+Grids cover ragged last boxes (np not a multiple of 32), more radial cells
+than the kernel's 32-plane rings and fewer, both outer boundaries.
+"""
+import numpy as np
+import pytest
+
+import pot3d_synth as syn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+BOXES = (0, 1, 32)
+
+
+@pytest.fixture(scope="module")
+def p3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_01126_gb300 import pot3d
+
+    pot3d.load(build_if_missing=True)
+    return pot3d
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+GRIDS = [
+    ((40, 40, 80), 1.0, "ylm", "source"),
+    ((13, 21, 37), 1.05, "bip", "source"),
+    ((9, 8, 64), 1.1, "bip", "source"),
+    ((49, 15, 45), 1.08, "bip", "source"),
+    ((3, 9, 40), 1.0, "bip", "source"),
+    ((12, 17, 40), 1.03, "bip", "closed"),
+    ((33, 19, 97), 1.06, "bip", "closed"),
+    ((70, 6, 33), 1.04, "bip", "source"),
+]
+
+
+def make_br(kind, nt, np_):
+    if kind == "ylm":
+        return syn.ylm_br(nt, np_, 3, 2)[0]
+    return syn.bipole_br(nt, np_, seed=1709, n_bipoles=30)
+
+
+def oracle_grid(oracle_mod, shape, ratio, outer="source"):
+    return oracle_mod.Grid(*shape, ratio=ratio, outer=outer, precond="ilu", blocks=BOXES)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape,ratio,kind,outer", GRIDS)
+def test_ilu_solve_parity(p3, oracle_mod, prec, shape, ratio, kind, outer):
+    nr, nt, np_ = shape
+    br = make_br(kind, nt, np_)
+    g = oracle_grid(oracle_mod, shape, ratio, outer)
+    ref, it_ref, st = g.solve(br, 1e-12)
+    assert st == oracle_mod.OK
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec, outer=outer, precond="ilu")
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(dev(br), 1e-12, phi)
+    x = host(phi)
+    b = g.rhs(br)
+    true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    if prec == "mixed":
+        assert true_rel <= 1.001e-12 and rel(x, ref) <= 1e-8, (true_rel, rel(x, ref))
+    else:
+        assert abs(it - it_ref) <= 1, (it, it_ref)
+        assert rel(x, ref) <= 1e-9, rel(x, ref)
+        assert true_rel <= 1e-12 + 2e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("shape,ratio", [((49, 15, 45), 1.08), ((7, 11, 70), 1.0)])
+def test_ilu_first_iterates(p3, oracle_mod, shape, ratio):
+    """x_1 = alpha_0 M^-1 b shows the preconditioner's application itself;
+    the next iterates follow the oracle's within rounding (1e-12 relative)."""
+    br = make_br("bip", shape[1], shape[2])
+    g = oracle_grid(oracle_mod, shape, ratio)
+    b = g.rhs(br)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for k in (1, 2, 5, 20):
+        x_ref, _, _ = g.pcg(b, 1e-300, maxit=k)
+        plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond="ilu", max_iters=k)
+        rc, it = plan.solve(dev(br), 1e-300, phi, check=False)
+        assert rc == p3.POT3D_ERR_NOT_CONVERGED and it == k
+        assert rel(host(phi), x_ref) <= 1e-12, (k, rel(host(phi), x_ref))
+        plan.close()
+
+
+def test_ilu_history_and_fewer_iterations(p3, oracle_mod):
+    """The residual history follows the oracle's (bar: 1e-6, the allowance
+    for substitutions that round differently: recurrences from a pivot
+    table against Saad's row-by-row factors); the same solution in fewer
+    iterations than diagonal scaling."""
+    shape, ratio = (17, 35, 129), 1.02
+    br = make_br("bip", 35, 129)
+    g = oracle_grid(oracle_mod, shape, ratio)
+    _, it_ref, _, h_ref = g.pcg(g.rhs(br), 1e-12, history=True)
+    plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond="ilu", history=1)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(dev(br), 1e-12, phi)
+    h = plan.history()
+    m = min(len(h), len(h_ref))
+    assert np.max(np.abs(h[:m] - h_ref[:m]) / h_ref[:m]) <= 1e-6
+    pj = p3.Plan(*shape, ratio=ratio, precision="fp64")
+    phj = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, itj = pj.solve(dev(br), 1e-12, phj)
+    assert it < 0.5 * itj, (it, itj)
+    assert rel(host(phi), host(phj)) <= 1e-9
+    plan.close()
+    pj.close()
+
+
+@pytest.mark.parametrize("arith", ["fp64", "f32"])
+def test_ilu_every_decomposition(p3, oracle_mod, arith):
+    """Every matvec variant keeps parity with PC2 (the matvec reads w in
+    place of r)."""
+    shape, ratio = (14, 37, 150), 1.03
+    br = make_br("bip", 37, 150)
+    g = oracle_grid(oracle_mod, shape, ratio)
+    ref, it_ref, _ = g.solve(br, 1e-12)
+    b = g.rhs(br)
+    prec = {"fp64": "fp64", "f32": "mixed"}[arith]
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    for v in range(len(p3.variants(arith))):
+        for chunks, rows in ((1, 16), (3, 150)):
+            plan = p3.Plan(*shape, ratio=ratio, precision=prec, precond="ilu")
+            plan.set_decomposition(arith, v, chunks, rows)
+            rc, it = plan.solve(dev(br), 1e-12 if prec == "fp64" else 1e-11, phi)
+            x = host(phi)
+            if prec == "fp64":
+                assert abs(it - it_ref) <= 1 and rel(x, ref) <= 1e-9, (v, chunks, it)
+            else:
+                assert np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b) <= 1e-11, (v, chunks)
+            plan.close()
+
+
+def test_ilu_unsupported_paths(p3):
+    br = torch.ones((7, 40), dtype=torch.float64, device="cuda")
+    plan = p3.Plan(6, 7, 40, precision="df", precond="ilu")
+    phi = torch.zeros((6, 7, 40), dtype=torch.float64, device="cuda")
+    rc, _ = plan.solve(br, 1e-10, phi, check=False)
+    assert rc == p3.POT3D_ERR_UNSUPPORTED
+    plan.close()
+    # a box of 32 phi columns would close the ring
+    plan = p3.Plan(6, 7, 32, precond="ilu")
+    rc, _ = plan.solve(torch.ones((7, 32), dtype=torch.float64, device="cuda"), 1e-10,
+                       torch.zeros((6, 7, 32), dtype=torch.float64, device="cuda"), check=False)
+    assert rc == p3.POT3D_ERR_UNSUPPORTED
+    plan.close()
+    with pytest.raises(p3.Pot3dError) as e:
+        p3.Batch(1 << 26, max_slots=1, precond="ilu")
+    assert e.value.code == p3.POT3D_ERR_UNSUPPORTED
+
+
+def test_ilu_first_iterates_full_size(p3, oracle_mod):
+    """151 x 301 x 601, the benchmark workload, in the launch configuration
+    bench.py times: the first 10 iterates against the oracle's (1e-12)."""
+    shape = (151, 301, 601)
+    br = syn.bipole_br(301, 601, seed=1709)
+    g = oracle_grid(oracle_mod, shape, 1.02)
+    x_ref, _, _ = g.pcg(g.rhs(br), 1e-300, maxit=10)
+    plan = p3.Plan(*shape, ratio=1.02, precision="fp64", precond="ilu", max_iters=10)
+    plan.autotune(0)
+    plan.set_opts(max_iters=10, precond="ilu")
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(dev(br), 1e-300, phi, check=False)
+    assert it == 10
+    assert rel(host(phi), x_ref) <= 1e-12, rel(host(phi), x_ref)
+    plan.close()
