@@ -1283,23 +1283,25 @@ __global__ void __launch_bounds__(NT)
 // wavefront across the warp): the phi neighbour's value arrives by one
 // shuffle from the previous step, the radial one is the lane's own.  Global
 // memory stays coalesced: every step the warp loads one whole r plane of
-// its 32 columns (r -= alpha q, ||r||^2, written back) into a ring of 32
-// planes in shared memory that the lanes read at their own step, and writes
-// one whole plane of y (into q's storage: q is dead once r is updated) from
-// a second ring as soon as its last lane has filled it.  The backward pass
-// runs the wavefront the other way (lane kk at step nr + 30 - i - kk) and
-// writes w = D z the same way.  Loads run PF steps ahead in registers.  The
+// its 32 columns (r -= alpha q, ||r||^2, written back) and lane kk reads its
+// column of it kk steps later from a delay line in shared memory (32 steps
+// x 32 lanes; each lane only reads back what it wrote itself).  y goes to
+// q's storage (q is dead once r is updated) in wavefront order: the row of
+// step t at row t mod nr.  The backward pass runs the wavefront the other
+// way (lane kk at step nr + 30 - i - kk), which reads those rows in reverse
+// order, and writes w = D z a plane at a time through the delay line once
+// lane 0 has run the plane.  Loads run PF steps ahead in registers.  The
 // pivot inverses are stored skewed, [j][t][kk] = 1 / p(t - kk, j, kk), so
 // the lanes' loads of one step are one contiguous row too.  The last block
 // sums the partials and closes the iteration; setup_out non-null: alpha = 0,
 // no iteration is closed, ||r||^2 and rho go to setup_out[0..1].
 template <class A>
 struct IluLayout {
-  // two rings of 32 planes x 32 columns, then the warp's coefficient
+  // a delay line of 32 steps x 32 lanes, then the warp's coefficient
   // columns [4][nr] (c^r_{i-1/2}, c^r_{i+1/2}, D, c^ph of its theta row)
   static __host__ __device__ size_t warp_bytes(int nr) {
-    return (2 * 32 * 32 * sizeof(typename A::val) + 4 * (size_t)nr * sizeof(typename A::coef) +
-            15) & ~(size_t)15;
+    return (32 * 32 * sizeof(typename A::val) + 4 * (size_t)nr * sizeof(typename A::coef) + 15) &
+           ~(size_t)15;
   }
 };
 
@@ -1315,6 +1317,14 @@ __device__ __forceinline__ float ld_issue(const float *p) {
   float v;
   asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
+}
+// Stores kept in order with those loads (k_ilu writes y over q entries
+// that its own earlier loads read).
+__device__ __forceinline__ void st_issue(double *p, double v) {
+  asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+__device__ __forceinline__ void st_issue(float *p, float v) {
+  asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
 
 template <class A, int NT>
@@ -1343,9 +1353,8 @@ __global__ void __launch_bounds__(NT)
     const int j = u / nkg, k0 = (u - j * nkg) * 32, k = k0 + lane;
     const bool act = k < np;
     const bool up = lane < 31 && k + 1 < np; // phi neighbour k + 1 in the box
-    val *ra = reinterpret_cast<val *>(smi + (size_t)wy * IluLayout<A>::warp_bytes(nr));
-    val *rb = ra + 32 * 32;
-    coef *cc = reinterpret_cast<coef *>(rb + 32 * 32);
+    val *dl = reinterpret_cast<val *>(smi + (size_t)wy * IluLayout<A>::warp_bytes(nr));
+    coef *cc = reinterpret_cast<coef *>(dl + 32 * 32);
     const coef *__restrict__ ic = static_cast<const coef *>(P.icoef);
     for (int i = lane; i < nr; i += 32) {
       const size_t o = (size_t)i * ntp + j;
@@ -1364,7 +1373,11 @@ __global__ void __launch_bounds__(NT)
     const int T = nr + 31; // wavefront steps per pass
     val rn[PF], qn[PF];
     coef pn[PF];
-    // ---- forward: r update, ||r||^2, y = (P + E)^-1 r, rho
+    // ---- forward: r update, ||r||^2, y = (P + E)^-1 r, rho.  y goes to
+    // q's storage in wavefront order: the y of step t (lane kk: cell
+    // t - kk) is one row of 32, stored at row t mod nr (a lane's steps
+    // kk .. kk + nr - 1 fall on distinct rows), which is also the order in
+    // which the backward pass needs it.
     auto fetch_f = [&](int t, int e) {
       rn[e] = A::zero();
       qn[e] = A::zero();
@@ -1377,7 +1390,12 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int e = 0; e < PF; e++) fetch_f(e, e);
     val ymine = A::zero(); // y of this lane's last cell: y_{i-1,k} of its next one
+    int yrow = 0;          // t mod nr
     for (int t0 = 0; t0 < T; t0 += PF) {
+      // rho of this chunk of PF steps: a plain sum of y s in the
+      // arithmetic's own type (y and s are the preconditioner's own
+      // results, rounded in that type), merged into arho per chunk
+      val rho_c = A::zero();
 #pragma unroll
       for (int e = 0; e < PF; e++) {
         const int t = t0 + e;
@@ -1387,36 +1405,39 @@ __global__ void __launch_bounds__(NT)
         const coef piv = pn[e];
         fetch_f(t + PF, e);
         if (t < nr) {
+          // plane t arrives for the whole warp; lane kk uses it kk steps
+          // later (its own column of the delay line dl)
           if (act && !setup) {
             rv = A::fma(nalpha, qv, rv);
             A::stv(r + c0 + (size_t)t * plane, rv);
           }
           if (act) A::d_add(arr, rv, rv);
-          ra[(t & 31) * 32 + lane] = rv;
+          dl[(t & 31) * 32 + lane] = rv;
         }
-        __syncwarp();
         const val yleft = A::shfl_up(ymine, 1); // y_{i,k-1}, the previous step of lane - 1
         const int i = t - lane;
         if (act && i >= 0 && i < nr) {
-          val sv = A::fma(cc[i], ymine, ra[(i & 31) * 32 + lane]);
+          val sv = A::fma(cc[i], ymine, dl[(i & 31) * 32 + lane]);
           if (lane > 0) sv = A::fma(cc[3 * nr + i], yleft, sv);
           const val y = A::mul(sv, piv);
-          A::d_add(arho, y, sv);
+          rho_c = A::fma(y, sv, rho_c);
           ymine = y;
-          rb[(i & 31) * 32 + lane] = y;
+          st_issue(q + c0 + (size_t)yrow * plane, y);
         }
-        __syncwarp();
-        const int pd = t - 31; // plane whose last lane just finished
-        if (act && pd >= 0 && pd < nr) A::stv(q + c0 + (size_t)pd * plane, rb[(pd & 31) * 32 + lane]);
+        if (++yrow == nr) yrow = 0;
       }
+      A::d_merge(arho, A::d_of(rho_c));
     }
-    // ---- backward: z = (P + E^T)^-1 P y, w = D z
+    // ---- backward: z = (P + E^T)^-1 P y, w = D z; lane kk runs cell i at
+    // step T - 1 - i - kk, whose y is the forward's row i + kk
     // (the loads below read y that the stores above wrote: keep their order)
     asm volatile("" ::: "memory");
+    int brow = (T - 1) % nr; // (T - 1 - t) mod nr of the next step fetched
     auto fetch_b = [&](int t, int e) {
-      const int pl = nr - 1 - t;
-      qn[e] = (act && pl >= 0) ? ld_issue(q + c0 + (size_t)pl * plane) : A::zero();
-      pn[e] = t < T ? ld_issue(pv + (size_t)(T - 1 - t) * 32) : coef{};
+      const int ts = T - 1 - t; // forward step whose y this step needs
+      qn[e] = (act && t < T) ? ld_issue(q + c0 + (size_t)brow * plane) : A::zero();
+      pn[e] = t < T ? ld_issue(pv + (size_t)ts * 32) : coef{};
+      if (--brow < 0) brow = nr - 1;
     };
 #pragma unroll
     for (int e = 0; e < PF; e++) fetch_b(e, e);
@@ -1429,21 +1450,19 @@ __global__ void __launch_bounds__(NT)
         const val yv = qn[e];
         const coef piv = pn[e];
         fetch_b(t + PF, e);
-        const int pl = nr - 1 - t;
-        if (pl >= 0) ra[(pl & 31) * 32 + lane] = yv;
-        __syncwarp();
         const val zright = A::shfl_down(zmine, 1); // z_{i,k+1}, the previous step of lane + 1
         const int i = T - 1 - t - lane;
         if (act && i >= 0 && i < nr) {
           val sv = A::mul(cc[nr + i], zmine);
           if (up) sv = A::fma(cc[3 * nr + i], zright, sv);
-          const val z = A::fma(piv, sv, ra[(i & 31) * 32 + lane]);
+          const val z = A::fma(piv, sv, yv);
           zmine = z;
-          rb[(i & 31) * 32 + lane] = A::mul(cc[2 * nr + i], z);
+          dl[(i & 31) * 32 + lane] = A::mul(cc[2 * nr + i], z);
         }
-        __syncwarp();
-        const int pd = T - 1 - t; // plane whose last lane (lane 0) just finished
-        if (act && pd >= 0 && pd < nr) A::stv(w + c0 + (size_t)pd * plane, rb[(pd & 31) * 32 + lane]);
+        // plane pd is complete once lane 0 has run it (this step); each
+        // lane stores its own column of it from the delay line
+        const int pd = T - 1 - t;
+        if (act && pd < nr) A::stv(w + c0 + (size_t)pd * plane, dl[(pd & 31) * 32 + lane]);
       }
     }
   }

@@ -7,6 +7,8 @@ Saad's ILU(0) and substitutes row by row; the GPU builds the pivots from the
 Grids cover ragged last boxes (np not a multiple of 32), more radial cells
 than the kernel's 32-plane rings and fewer, both outer boundaries.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -105,20 +107,35 @@ def test_ilu_first_iterates(p3, oracle_mod, shape, ratio):
 
 
 def test_ilu_history_and_fewer_iterations(p3, oracle_mod):
-    """The residual history follows the oracle's (bar: 1e-6, the allowance
-    for substitutions that round differently: recurrences from a pivot
-    table against Saad's row-by-row factors); the same solution in fewer
-    iterations than diagonal scaling."""
+    """The residual history follows the oracle's; the same solution in
+    fewer iterations than diagonal scaling.
+
+    History bar: 4 x the oracle's own spread under other thread counts
+    (other reduction orders; measured 1.7e-6 here, oracle 213 iterations
+    with every thread count), and at least 1e-6, the allowance for
+    substitutions that round differently (recurrences from a pivot table
+    against Saad's row-by-row factors)."""
     shape, ratio = (17, 35, 129), 1.02
     br = make_br("bip", 35, 129)
     g = oracle_grid(oracle_mod, shape, ratio)
-    _, it_ref, _, h_ref = g.pcg(g.rhs(br), 1e-12, history=True)
+    b = g.rhs(br)
+    n = os.cpu_count() or 1
+    oracle_mod.set_threads(n)
+    _, it_ref, _, h_ref = g.pcg(b, 1e-12, history=True)
+    spread = 0.0
+    for t in sorted({1, 2, 3} - {n}):
+        oracle_mod.set_threads(t)
+        _, _, _, h_t = g.pcg(b, 1e-12, history=True)
+        m = min(len(h_t), len(h_ref))
+        spread = max(spread, np.max(np.abs(h_t[:m] - h_ref[:m]) / h_ref[:m]))
+    oracle_mod.set_threads(n)
     plan = p3.Plan(*shape, ratio=ratio, precision="fp64", precond="ilu", history=1)
     phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, it = plan.solve(dev(br), 1e-12, phi)
     h = plan.history()
     m = min(len(h), len(h_ref))
-    assert np.max(np.abs(h[:m] - h_ref[:m]) / h_ref[:m]) <= 1e-6
+    dev_h = np.max(np.abs(h[:m] - h_ref[:m]) / h_ref[:m])
+    assert dev_h <= max(1e-6, 4.0 * spread), (dev_h, spread)
     pj = p3.Plan(*shape, ratio=ratio, precision="fp64")
     phj = torch.zeros(shape, dtype=torch.float64, device="cuda")
     rc, itj = pj.solve(dev(br), 1e-12, phj)
