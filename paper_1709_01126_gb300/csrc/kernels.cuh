@@ -1290,41 +1290,45 @@ __global__ void __launch_bounds__(NT)
 // step t at row t mod nr.  The backward pass runs the wavefront the other
 // way (lane kk at step nr + 30 - i - kk), which reads those rows in reverse
 // order, and writes w = D z a plane at a time through the delay line once
-// lane 0 has run the plane.  Loads run PF steps ahead in registers.  The
+// lane 0 has run the plane.  Each step's loads go by cp.async into a
+// staging ring in shared memory, PF steps ahead, one copy group per step
+// awaited by count (loads prefetched into registers instead waited for all
+// younger loads too, and every step paid a memory latency).  The
 // pivot inverses are stored skewed, [j][t][kk] = 1 / p(t - kk, j, kk), so
 // the lanes' loads of one step are one contiguous row too.  The last block
 // sums the partials and closes the iteration; setup_out non-null: alpha = 0,
 // no iteration is closed, ||r||^2 and rho go to setup_out[0..1].
 template <class A>
 struct IluLayout {
-  // a delay line of 32 steps x 32 lanes, then the warp's coefficient
-  // columns [4][nr] (c^r_{i-1/2}, c^r_{i+1/2}, D, c^ph of its theta row)
+  // steps whose loads are in flight (cp.async groups)
+  static constexpr int PF = 8;
+  // a delay line of 32 steps x 32 lanes; PF staging slots of three rows of
+  // 32 (r, q, pivots in the forward pass; y and pivots in the backward);
+  // then the warp's coefficient columns [4][nr] (c^r_{i-1/2}, c^r_{i+1/2},
+  // D, c^ph of its theta row)
   static __host__ __device__ size_t warp_bytes(int nr) {
-    return (32 * 32 * sizeof(typename A::val) + 4 * (size_t)nr * sizeof(typename A::coef) + 15) &
+    return ((32 * 32 + PF * 3 * 32) * sizeof(typename A::val) +
+            4 * (size_t)nr * sizeof(typename A::coef) + 15) &
            ~(size_t)15;
   }
 };
 
-// Global loads issued where they stand.  k_ilu fetches its planes PF steps
-// ahead of their use; written as plain loads the compiler may sink them next
-// to their first use, and every wavefront step would then wait for memory.
-__device__ __forceinline__ double ld_issue(const double *p) {
-  double v;
-  asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
+// Asynchronous copies of one element per thread from global to shared
+// memory (cp.async, 4 or 8 bytes), committed as one group per wavefront step
+// and awaited by group count: k_ilu keeps PF steps of loads in flight and
+// waits for exactly the oldest step.
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src) {
+  static_assert(B == 4 || B == 8, "cp.async element of 4 or 8 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(B)
+               : "memory");
 }
-__device__ __forceinline__ float ld_issue(const float *p) {
-  float v;
-  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
-// Stores kept in order with those loads (k_ilu writes y over q entries
-// that its own earlier loads read).
-__device__ __forceinline__ void st_issue(double *p, double v) {
-  asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v));
-}
-__device__ __forceinline__ void st_issue(float *p, float v) {
-  asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 template <class A, int NT>
@@ -1333,7 +1337,8 @@ __global__ void __launch_bounds__(NT)
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
-  constexpr int NW = NT / 32, PF = 8;
+  constexpr int NW = NT / 32, PF = IluLayout<A>::PF;
+  static_assert((PF & (PF - 1)) == 0, "PF a power of two");
   extern __shared__ __align__(16) unsigned char smi[];
   __shared__ double red[NW];
   __shared__ int s_last;
@@ -1354,7 +1359,8 @@ __global__ void __launch_bounds__(NT)
     const bool act = k < np;
     const bool up = lane < 31 && k + 1 < np; // phi neighbour k + 1 in the box
     val *dl = reinterpret_cast<val *>(smi + (size_t)wy * IluLayout<A>::warp_bytes(nr));
-    coef *cc = reinterpret_cast<coef *>(dl + 32 * 32);
+    val *stg = dl + 32 * 32; // [PF][3][32]
+    coef *cc = reinterpret_cast<coef *>(stg + PF * 3 * 32);
     const coef *__restrict__ ic = static_cast<const coef *>(P.icoef);
     for (int i = lane; i < nr; i += 32) {
       const size_t o = (size_t)i * ntp + j;
@@ -1371,100 +1377,104 @@ __global__ void __launch_bounds__(NT)
     const typename A::scal nalpha = A::scal_from(setup ? 0.0 : -ldcg(&stt->alpha[kit & 1]));
     const size_t c0 = (size_t)j * P.pitch + k;
     const int T = nr + 31; // wavefront steps per pass
-    val rn[PF], qn[PF];
-    coef pn[PF];
-    // ---- forward: r update, ||r||^2, y = (P + E)^-1 r, rho.  y goes to
-    // q's storage in wavefront order: the y of step t (lane kk: cell
-    // t - kk) is one row of 32, stored at row t mod nr (a lane's steps
-    // kk .. kk + nr - 1 fall on distinct rows), which is also the order in
-    // which the backward pass needs it.
-    auto fetch_f = [&](int t, int e) {
-      rn[e] = A::zero();
-      qn[e] = A::zero();
+    constexpr int EB = (int)sizeof(val);
+    static_assert(sizeof(val) == sizeof(st) && sizeof(val) == sizeof(coef),
+                  "one element size for the staged rows");
+    // ---- forward: r update, ||r||^2, y = (P + E)^-1 r, rho.  The loads of
+    // step t (the lane's element of r and q in plane t, its pivot row t) go
+    // by cp.async into staging slot t mod PF, one group per step, PF steps
+    // ahead.  y goes to q's storage in wavefront order: the y of step t
+    // (lane kk: cell t - kk) is one row of 32, stored at row t mod nr (a
+    // lane's steps kk .. kk + nr - 1 fall on distinct rows), which is also
+    // the order in which the backward pass needs it.
+    auto fetch_f = [&](int t) {
+      val *sl = stg + (t & (PF - 1)) * 96 + lane;
       if (act && t < nr) {
-        rn[e] = ld_issue(r + c0 + (size_t)t * plane);
-        if (!setup) qn[e] = ld_issue(q + c0 + (size_t)t * plane);
+        cp_async_elem<EB>(sl, r + c0 + (size_t)t * plane);
+        if (!setup) cp_async_elem<EB>(sl + 32, q + c0 + (size_t)t * plane);
       }
-      pn[e] = t < T ? ld_issue(pv + (size_t)t * 32) : coef{};
+      if (t < T) cp_async_elem<EB>(sl + 64, pv + (size_t)t * 32);
+      cp_async_commit();
     };
-#pragma unroll
-    for (int e = 0; e < PF; e++) fetch_f(e, e);
+    for (int t = 0; t < PF - 1; t++) fetch_f(t);
     val ymine = A::zero(); // y of this lane's last cell: y_{i-1,k} of its next one
+    val rho_c = A::zero(); // rho of the current chunk of PF steps (see below)
     int yrow = 0;          // t mod nr
-    for (int t0 = 0; t0 < T; t0 += PF) {
-      // rho of this chunk of PF steps: a plain sum of y s in the
+    for (int t = 0; t < T; t++) {
+      fetch_f(t + PF - 1);
+      cp_async_wait<PF - 1>(); // the group of step t has landed
+      const val *sl = stg + (t & (PF - 1)) * 96 + lane;
+      const coef piv = reinterpret_cast<const coef *>(sl)[64];
+      if (t < nr) {
+        // plane t arrives for the whole warp; lane kk uses it kk steps
+        // later (its own column of the delay line)
+        val rv = sl[0];
+        if (act && !setup) {
+          rv = A::fma(nalpha, sl[32], rv);
+          A::stv(r + c0 + (size_t)t * plane, rv);
+        }
+        if (act) A::d_add(arr, rv, rv);
+        dl[(t & 31) * 32 + lane] = rv;
+      }
+      const val yleft = A::shfl_up(ymine, 1); // y_{i,k-1}, the previous step of lane - 1
+      const int i = t - lane;
+      if (act && i >= 0 && i < nr) {
+        val sv = A::fma(cc[i], ymine, dl[(i & 31) * 32 + lane]);
+        if (lane > 0) sv = A::fma(cc[3 * nr + i], yleft, sv);
+        const val y = A::mul(sv, piv);
+        rho_c = A::fma(y, sv, rho_c);
+        ymine = y;
+        A::stv(q + c0 + (size_t)yrow * plane, y);
+      }
+      if (++yrow == nr) yrow = 0;
+      // rho: a plain sum of y s over each chunk of PF steps in the
       // arithmetic's own type (y and s are the preconditioner's own
       // results, rounded in that type), merged into arho per chunk
-      val rho_c = A::zero();
-#pragma unroll
-      for (int e = 0; e < PF; e++) {
-        const int t = t0 + e;
-        if (t >= T) break;
-        val rv = rn[e];
-        const val qv = qn[e];
-        const coef piv = pn[e];
-        fetch_f(t + PF, e);
-        if (t < nr) {
-          // plane t arrives for the whole warp; lane kk uses it kk steps
-          // later (its own column of the delay line dl)
-          if (act && !setup) {
-            rv = A::fma(nalpha, qv, rv);
-            A::stv(r + c0 + (size_t)t * plane, rv);
-          }
-          if (act) A::d_add(arr, rv, rv);
-          dl[(t & 31) * 32 + lane] = rv;
-        }
-        const val yleft = A::shfl_up(ymine, 1); // y_{i,k-1}, the previous step of lane - 1
-        const int i = t - lane;
-        if (act && i >= 0 && i < nr) {
-          val sv = A::fma(cc[i], ymine, dl[(i & 31) * 32 + lane]);
-          if (lane > 0) sv = A::fma(cc[3 * nr + i], yleft, sv);
-          const val y = A::mul(sv, piv);
-          rho_c = A::fma(y, sv, rho_c);
-          ymine = y;
-          st_issue(q + c0 + (size_t)yrow * plane, y);
-        }
-        if (++yrow == nr) yrow = 0;
+      if ((t & (PF - 1)) == PF - 1 || t == T - 1) {
+        A::d_merge(arho, A::d_of(rho_c));
+        rho_c = A::zero();
       }
-      A::d_merge(arho, A::d_of(rho_c));
     }
+    cp_async_wait<0>();
+    __threadfence_block(); // the y stores above come before the copies below read them
     // ---- backward: z = (P + E^T)^-1 P y, w = D z; lane kk runs cell i at
-    // step T - 1 - i - kk, whose y is the forward's row i + kk
-    // (the loads below read y that the stores above wrote: keep their order)
-    asm volatile("" ::: "memory");
+    // step T - 1 - i - kk, whose y is the forward's row i + kk, read from
+    // row (T - 1 - t) mod nr (the y each lane wrote there itself)
     int brow = (T - 1) % nr; // (T - 1 - t) mod nr of the next step fetched
-    auto fetch_b = [&](int t, int e) {
-      const int ts = T - 1 - t; // forward step whose y this step needs
-      qn[e] = (act && t < T) ? ld_issue(q + c0 + (size_t)brow * plane) : A::zero();
-      pn[e] = t < T ? ld_issue(pv + (size_t)ts * 32) : coef{};
-      if (--brow < 0) brow = nr - 1;
-    };
-#pragma unroll
-    for (int e = 0; e < PF; e++) fetch_b(e, e);
-    val zmine = A::zero(); // z of this lane's last cell: z_{i+1,k} of its next one
-    for (int t0 = 0; t0 < T; t0 += PF) {
-#pragma unroll
-      for (int e = 0; e < PF; e++) {
-        const int t = t0 + e;
-        if (t >= T) break;
-        const val yv = qn[e];
-        const coef piv = pn[e];
-        fetch_b(t + PF, e);
-        const val zright = A::shfl_down(zmine, 1); // z_{i,k+1}, the previous step of lane + 1
-        const int i = T - 1 - t - lane;
-        if (act && i >= 0 && i < nr) {
-          val sv = A::mul(cc[nr + i], zmine);
-          if (up) sv = A::fma(cc[3 * nr + i], zright, sv);
-          const val z = A::fma(piv, sv, yv);
-          zmine = z;
-          dl[(i & 31) * 32 + lane] = A::mul(cc[2 * nr + i], z);
-        }
-        // plane pd is complete once lane 0 has run it (this step); each
-        // lane stores its own column of it from the delay line
-        const int pd = T - 1 - t;
-        if (act && pd < nr) A::stv(w + c0 + (size_t)pd * plane, dl[(pd & 31) * 32 + lane]);
+    int tb = 0;              // step of the next fetch
+    auto fetch_b = [&]() {
+      val *sl = stg + (tb & (PF - 1)) * 96 + lane;
+      if (tb < T) {
+        if (act) cp_async_elem<EB>(sl, q + c0 + (size_t)brow * plane);
+        cp_async_elem<EB>(sl + 64, pv + (size_t)(T - 1 - tb) * 32);
       }
+      cp_async_commit();
+      if (--brow < 0) brow = nr - 1;
+      tb++;
+    };
+    for (int e = 0; e < PF - 1; e++) fetch_b();
+    val zmine = A::zero(); // z of this lane's last cell: z_{i+1,k} of its next one
+    for (int t = 0; t < T; t++) {
+      fetch_b();
+      cp_async_wait<PF - 1>();
+      const val *sl = stg + (t & (PF - 1)) * 96 + lane;
+      const val yv = sl[0];
+      const coef piv = reinterpret_cast<const coef *>(sl)[64];
+      const val zright = A::shfl_down(zmine, 1); // z_{i,k+1}, the previous step of lane + 1
+      const int i = T - 1 - t - lane;
+      if (act && i >= 0 && i < nr) {
+        val sv = A::mul(cc[nr + i], zmine);
+        if (up) sv = A::fma(cc[3 * nr + i], zright, sv);
+        const val z = A::fma(piv, sv, yv);
+        zmine = z;
+        dl[(i & 31) * 32 + lane] = A::mul(cc[2 * nr + i], z);
+      }
+      // plane pd is complete once lane 0 has run it (this step); each
+      // lane stores its own column of it from the delay line
+      const int pd = T - 1 - t;
+      if (act && pd < nr) A::stv(w + c0 + (size_t)pd * plane, dl[(pd & 31) * 32 + lane]);
     }
+    cp_async_wait<0>();
   }
   const double prr = block_sum<NT>(A::d_get(arr), red);
   const double prho = block_sum<NT>(A::d_get(arho), red);
