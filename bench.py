@@ -493,7 +493,7 @@ def run_gpu(args):
     return 0
 
 
-def precond_record(pot3d, torch, dev, br_d, steps=2):
+def precond_record(pot3d, torch, dev, br_d, steps=1):
     """Time to solution of the same 151x301x601 solve to 1e-10 with diagonal
     scaling (PC1, the paper's), with the line preconditioners (phi lines,
     radial lines, both directions) and with PC2 (the paper's subdomain

@@ -401,3 +401,28 @@ def test_residual_history_matches_oracle(p3, oracle_mod, prec, factor):
     with pytest.raises(p3.Pot3dError):
         plan.history()
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df", "mixed"])
+@pytest.mark.parametrize("shape", [(5, 7, 700), (4, 5, 1601), (6, 9, 321)])
+def test_long_rows_keep_parity(p3, oracle_mod, prec, shape):
+    """Rows longer than one update unit (the register-staged update takes
+    640 FP32 or 320 double-float elements per unit, the bulk-copy update
+    2560 bytes per segment): several units per row, a ragged last one."""
+    nr, nt, np_ = shape
+    br = make_br("bip", nt, np_)
+    g = oracle_mod.Grid(*shape, ratio=1.04)
+    ref, it_ref, st = g.solve(br, 1e-12)
+    assert st == oracle_mod.OK
+    plan = p3.Plan(*shape, ratio=1.04, precision=prec)
+    phi = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(dev(br), 1e-12, phi)
+    x = host(phi)
+    b = g.rhs(br)
+    true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    if prec == "mixed":
+        assert true_rel <= 1.001e-12 and rel(x, ref) <= 1e-8, (true_rel, rel(x, ref))
+    else:
+        assert abs(it - it_ref) <= 1, (it, it_ref)
+        assert rel(x, ref) <= 1e-9, rel(x, ref)
+    plan.close()
