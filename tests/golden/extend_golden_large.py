@@ -8,6 +8,11 @@
                     the stored main thread count, so the same iterates as the
                     stored sample, which is checked) and the true residual
                     ||b - L Phi|| / ||b|| of its result
+  --precond PC ...  the solve to 1e-10 with the oracle's preconditioner PC
+                    ("philine", "rline", "lines", "ilu"; PC2 with its default
+                    boxes): stopping iteration, Phi on the stored sample and
+                    the true residual under the main thread count, and the
+                    stopping iteration under each --stop-threads count
 
 Several processes may run at once (different thread counts); each updates
 the file under a lock.  Run from the repo root, e.g.
@@ -47,6 +52,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, nargs="*", default=[])
     ap.add_argument("--true-residual", action="store_true")
+    ap.add_argument("--precond", nargs="*", default=[])
+    ap.add_argument("--stop-threads", type=int, nargs="*", default=[])
     args = ap.parse_args()
     with open(PATH) as f:
         gold = json.load(f)
@@ -74,6 +81,24 @@ def main():
             tr = float(np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b))
             update(lambda gd: gd["tol_%g" % tol].__setitem__("true_relres", tr))
             print("tol %g: true residual %.3e" % (tol, tr), flush=True)
+    for pc in args.precond:
+        gp = oracle.Grid(*SHAPE, ratio=RATIO, precond=pc)
+        main_t = gold["relres_history"]["threads"]
+        oracle.set_threads(main_t)
+        x, it, st = gp.pcg(b, 1e-10)
+        assert st == oracle.OK
+        tr = float(np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b))
+        rec = {"tol": 1e-10, "iters": it, "threads": main_t, "true_relres": tr,
+               "sample_phi": x.ravel()[gold["sample_index"]].tolist(), "other_stops": {}}
+        if pc == "ilu":
+            rec["blocks"] = list(gp.blocks)
+        for nth in args.stop_threads:
+            oracle.set_threads(nth)
+            _, it_t, _ = gp.pcg(b, 1e-10)
+            rec["other_stops"][str(oracle.get_threads())] = it_t
+        update(lambda gd: gd.setdefault("precond", {}).__setitem__(pc, rec))
+        print("precond %s: %d iterations, true residual %.3e, other stops %s"
+              % (pc, it, tr, rec["other_stops"]), flush=True)
 
 
 if __name__ == "__main__":

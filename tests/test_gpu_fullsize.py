@@ -9,6 +9,9 @@ times.
     boundary-folded layer: inner and source-surface layers, both pole rings,
     the phi-wrap columns), the stopping iteration, the whole residual
     history, and the true residual recomputed by the oracle's operator;
+  * full FP64 solves to 1e-10 with phi lines, both line directions, PC2 and
+    radial lines against the stored oracle solves with the same
+    preconditioner;
 - 401 x 801 x 1601 (514 M unknowns, the largest single-GPU case): the first
   200 iterates against the oracle's.
 
@@ -257,3 +260,33 @@ def test_c3_first_200_iterates(p3, oracle_mod):
         d = rel(phi.cpu().numpy(), x)
         assert d <= 4.0 * ARITH_FACTOR[prec] * max(spread, 1e-14), (prec, d, spread)
         plan.close()
+
+
+@pytest.mark.parametrize("pc", ["philine", "lines", "ilu", "rline"])
+def test_c2_preconditioned_full_solve(p3, oracle_mod, c2, gold, pc):
+    """151 x 301 x 601 to 1e-10 in FP64 with each stronger preconditioner
+    (phi lines, both line directions, PC2, radial lines), in the benchmark's
+    kernel configuration, against the oracle's solve with the same
+    preconditioner (stored by extend_golden_large.py --precond): the stopping
+    iteration within +-1 of the oracle's stops under its stored reduction
+    orders, Phi on the stratified sample within 1e-9, and the true residual
+    (recomputed by the oracle) within 4 x the larger of tol and the oracle's
+    own true residual at its stop."""
+    rec = gold.get("precond", {}).get(pc)
+    if rec is None:
+        pytest.skip("no stored oracle solve with %s" % pc)
+    g, br, b = c2
+    plan = p3.Plan(*C2, ratio=1.02, precision="fp64", precond=pc)
+    plan.autotune(0)
+    plan.set_opts(precond=pc)
+    phi = torch.zeros(C2, dtype=torch.float64, device="cuda")
+    rc, it = plan.solve(torch.from_numpy(br).cuda(), rec["tol"], phi)
+    stops = [rec["iters"]] + list(rec["other_stops"].values())
+    assert min(stops) - 1 <= it <= max(stops) + 1, (it, stops)
+    x = phi.cpu().numpy()
+    xs = x.ravel()[gold["sample_index"]]
+    rs = np.array(rec["sample_phi"])
+    assert np.linalg.norm(xs - rs) / np.linalg.norm(rs) <= 1e-9
+    true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+    assert true_rel <= 4.0 * max(rec["tol"], rec["true_relres"]), (true_rel, rec["true_relres"])
+    plan.close()
