@@ -6,14 +6,17 @@
  *   - Sec. 2.1, Eq. 1: Laplace equation for the scalar potential Phi,
  *     B = grad Phi.
  *   - Sec. 2.1, Eq. 2: inner boundary dPhi/dr = Br at r = r0 (the photosphere).
- *   - Sec. 2.1: outer boundary "source surface" Phi = 0 at r = r1; phi periodic.
+ *   - Sec. 2.1: outer boundary "source surface" Phi = 0 at r = r1, or the
+ *     closed wall Br = 0 there; phi periodic.
  *   - Sec. 2.1, Eq. 3: polar boundary value = phi-average of Phi half a cell
  *     from the pole.
  *   - Sec. 2.2 and Eq. 4: second-order 7-point finite-difference operator on
  *     a logically rectangular grid, nonuniform in r and theta, here in its
  *     symmetric volume-weighted form (the r^2 metric factors restored).
  *   - Sec. 2.3: preconditioned conjugate gradient with point-Jacobi /
- *     diagonal scaling (PC1).
+ *     diagonal scaling (PC1) or with the non-overlapping domain
+ *     decomposition with ILU(0) per subdomain (PC2); line preconditioners
+ *     beside them, of the vectorisable kind Sec. 6 asks for.
  *
  * Grid convention: Phi is cell-centred in r, theta and phi.  Unknowns are
  * Phi[i][j][k], i < nr (r), j < nt (theta, from the north pole), k < np
