@@ -17,7 +17,12 @@
 //              stencil with the boundary conditions folded into the metric
 //              tables, sigma partial; the last block to finish forms alpha.
 //   k_update : r update, ||r||^2 and rho partials; the last block forms the
-//              relative residual, the convergence flag and beta.
+//              relative residual, the convergence flag and beta (bulk copies
+//              into shared memory; with the phi-line preconditioner also the
+//              ring solve).  k_update_rs is the same update with rows staged
+//              in registers (diagonal scaling in double-float and FP32);
+//              k_rline (radial lines) and k_ilu (PC2, subdomain ILU(0)) take
+//              its place with those preconditioners.
 // Every reduction is deterministic: each work item writes its partial to a
 // fixed slot, and the last block sums the slots in a fixed order.
 #pragma once
