@@ -138,3 +138,29 @@ def test_batch_phi_line_matches_solve_mixed(p3, oracle_mod):
         g = oracle_mod.Grid(*pl.shape, ratio=1.03)
         b = g.rhs(br.cpu().numpy())
         assert np.linalg.norm(b - g.apply(mixed[u])) / np.linalg.norm(b) <= 1.01e-10
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "philine"])
+def test_batch_closed_wall_in_a_mix(p3, oracle_mod, precond):
+    """Closed-wall plans (Br = 0 at r1: balanced Br, zero-mean gauge) batched
+    together with source-surface plans: each gives the bits of
+    pot3d_solve_mixed, its mean is zero, and the oracle's FP64 residual of
+    the balanced system meets the tolerance."""
+    outers = ["closed", "source", "closed", "source"]
+    plans = [p3.Plan(*g, ratio=1.03, precision="mixed", outer=o, precond=precond)
+             for g, o in zip(GRIDS, outers)]
+    brs = [torch.from_numpy(syn.bipole_br(g[1], g[2], seed=70 + u, n_bipoles=15) + 0.3).cuda()
+           for u, g in enumerate(GRIDS)]
+    mixed, info = run_batch(p3, plans, brs, precond=precond)
+    for u, (pl, br, o) in enumerate(zip(plans, brs, outers)):
+        st, outer, inner, rr = info[u]
+        assert st == 0 and rr <= 1e-10
+        phi = torch.zeros(pl.shape, dtype=torch.float64, device="cuda")
+        rc, o2, i2 = pl.solve_mixed(br, 1e-10, phi)
+        assert (o2, i2) == (outer, inner)
+        assert np.array_equal(phi.cpu().numpy(), mixed[u])
+        g = oracle_mod.Grid(*pl.shape, ratio=1.03, outer=o)
+        b = g.rhs(br.cpu().numpy())
+        assert np.linalg.norm(b - g.apply(mixed[u])) / np.linalg.norm(b) <= 1.01e-10
+        if o == "closed":
+            assert abs(mixed[u].mean()) <= 1e-12 * np.abs(mixed[u]).max()

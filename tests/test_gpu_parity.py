@@ -426,3 +426,34 @@ def test_long_rows_keep_parity(p3, oracle_mod, prec, shape):
         assert abs(it - it_ref) <= 1, (it, it_ref)
         assert rel(x, ref) <= 1e-9, rel(x, ref)
     plan.close()
+
+
+@pytest.mark.parametrize("pc", ["philine", "rline", "lines", "ilu"])
+@pytest.mark.parametrize("outer", ["source", "closed"])
+def test_explicit_faces_every_preconditioner(p3, oracle_mod, pc, outer):
+    """Explicit nonuniform r and theta faces with each stronger
+    preconditioner and both outer boundaries: every preconditioner builds
+    its tables (ring factors, column factors, PC2 pivots) from the plan's
+    own coefficients, which here come from the given faces."""
+    nr, nt, np_ = 11, 17, 40
+    rf = 1.0 + 1.5 * (np.linspace(0, 1, nr + 1) ** 1.3)
+    u = np.linspace(0, 1, nt + 1)
+    tf = np.pi * (u + 0.12 * np.sin(2 * np.pi * u) / (2 * np.pi))
+    tf[0], tf[-1] = 0.0, np.pi
+    br = make_br("bip", nt, np_)
+    g = oracle_mod.Grid(nr, nt, np_, r_faces=rf, t_faces=tf, outer=outer, precond=pc)
+    ref, it_ref, st = g.solve(br, 1e-12)
+    assert st == oracle_mod.OK
+    for prec in ("fp64", "mixed"):
+        plan = p3.Plan(nr, nt, np_, r_faces=rf, t_faces=tf, precision=prec, outer=outer,
+                       precond=pc)
+        phi = torch.zeros((nr, nt, np_), dtype=torch.float64, device="cuda")
+        rc, it = plan.solve(dev(br), 1e-12, phi)
+        x = host(phi)
+        if prec == "fp64":
+            assert abs(it - it_ref) <= 1 and rel(x, ref) <= 1e-9, (prec, it, it_ref, rel(x, ref))
+        else:
+            b = g.rhs(br)
+            true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
+            assert true_rel <= 1.001e-12 and rel(x, ref) <= 1e-8, (true_rel, rel(x, ref))
+        plan.close()
