@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(NT)
   using val = typename A::val;
   using st = typename A::st;
   using coef = typename A::coef;
-  constexpr int NW = NT / 32, PF = 4;
+  constexpr int NW = NT / 32, PF = 8;
   __shared__ double red[NW];
   __shared__ int s_last;
   const ProbDev &P = probs[0];
