@@ -992,7 +992,9 @@ __global__ void __launch_bounds__(NT)
 // (every row access of the warp is one contiguous segment), 8 warps per
 // block.  The forward pass keeps y in q's storage (q is dead once r is
 // updated; the next matvec rewrites it), the backward pass reads it back in
-// reverse order (mostly from L2).  ADD = false: the kernel is the whole
+// reverse order (mostly from L2).  Each thread loads PF = 8 planes of its
+// column at a time before it runs them (four measured 4-7% slower in the
+// mixed solves).  ADD = false: the kernel is the whole
 // update of the iteration (r -= alpha q, ||r||^2, radial-line rho, w) and
 // closes it.  ADD = true (both line directions): the phi-line update ran
 // first (r updated, w holds D (T_phi^-1 - D^-1) r, ||r||^2 and its rho
