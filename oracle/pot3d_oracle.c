@@ -362,32 +362,41 @@ static void precond_philine(const orc_op *op, const double *r, double *z) {
 static void precond_rline(const orc_op *op, const double *r, double *z) {
   const int nr = op->nr, nt = op->nt, np = op->np;
   const long plane = (long)nt * np;
+  /* The coefficients of a column depend on (i, j) only, so the columns of
+     one theta row are eliminated together, plane by plane (contiguous
+     accesses); each column still goes through the same operations in the
+     same order as a column-by-column Thomas solve. */
 #pragma omp parallel
   {
-    double *cp = malloc(sizeof(double) * nr); /* modified super-diagonal */
-    double *dp = malloc(sizeof(double) * nr); /* modified right-hand side */
+    double *cp = malloc(sizeof(double) * nr);            /* modified super-diagonal */
+    double *dp = malloc(sizeof(double) * (long)nr * np); /* modified right-hand sides */
 #pragma omp for schedule(static)
-    for (long col = 0; col < plane; col++) {
-      const int j = (int)(col / np);
+    for (int j = 0; j < nt; j++) {
       /* row i: a_i z_{i-1} + b_i z_i + c_i z_{i+1} = r_i with
          a_i = -cr[i-1][j], b_i = diag[i][j], c_i = -cr[i][j] */
       for (int i = 0; i < nr; i++) {
         const double a = (i > 0) ? -op->cr[(i - 1) * nt + j] : 0.0;
         const double b = op->diag[i * nt + j];
         const double c = (i < nr - 1) ? -op->cr[i * nt + j] : 0.0;
-        const double ri = r[(long)i * plane + col];
+        const double *ri = r + (long)i * plane + (long)j * np;
+        double *di = dp + (long)i * np;
         if (i == 0) {
           cp[0] = c / b;
-          dp[0] = ri / b;
+          for (int k = 0; k < np; k++) di[k] = ri[k] / b;
         } else {
           const double m = b - a * cp[i - 1];
           cp[i] = c / m;
-          dp[i] = (ri - a * dp[i - 1]) / m;
+          const double *dm = dp + (long)(i - 1) * np;
+          for (int k = 0; k < np; k++) di[k] = (ri[k] - a * dm[k]) / m;
         }
       }
-      z[(long)(nr - 1) * plane + col] = dp[nr - 1];
-      for (int i = nr - 2; i >= 0; i--)
-        z[(long)i * plane + col] = dp[i] - cp[i] * z[(long)(i + 1) * plane + col];
+      double *zl = z + (long)(nr - 1) * plane + (long)j * np;
+      for (int k = 0; k < np; k++) zl[k] = dp[(long)(nr - 1) * np + k];
+      for (int i = nr - 2; i >= 0; i--) {
+        double *zi = z + (long)i * plane + (long)j * np;
+        const double *zn = zi + plane;
+        for (int k = 0; k < np; k++) zi[k] = dp[(long)i * np + k] - cp[i] * zn[k];
+      }
     }
     free(cp);
     free(dp);
