@@ -457,3 +457,39 @@ def test_explicit_faces_every_preconditioner(p3, oracle_mod, pc, outer):
             true_rel = np.linalg.norm(b - g.apply(x)) / np.linalg.norm(b)
             assert true_rel <= 1.001e-12 and rel(x, ref) <= 1e-8, (true_rel, rel(x, ref))
         plan.close()
+
+
+@pytest.mark.parametrize("pc", ["philine", "rline", "lines", "ilu"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_initial_guess_every_preconditioner(p3, oracle_mod, pc, prec):
+    """A solve started from a given Phi (opts.use_x0, also what verify's
+    restarts use) with each stronger preconditioner: from the oracle's
+    solution it stops at once (FP64) or keeps it (mixed), from the oracle's
+    5th PCG iterate (with the same preconditioner) it reaches the oracle's
+    solution (the preconditioners' setup launches run on the residual of the
+    given Phi)."""
+    shape, ratio = (12, 16, 40), 1.05
+    br = make_br("bip", 16, 40)
+    g = oracle_mod.Grid(*shape, ratio=ratio, precond=pc)
+    ref, it_ref, _ = g.solve(br, 1e-12)
+    plan = p3.Plan(*shape, ratio=ratio, precision=prec, use_x0=1, precond=pc)
+    phi = dev(ref)
+    if prec == "mixed":
+        rc, outer, it = plan.solve_mixed(dev(br), 1e-12, phi)
+    else:
+        rc, it = plan.solve(dev(br), 1e-12, phi)
+    if prec == "fp64":
+        assert it <= 2, it
+        assert rel(host(phi), ref) <= 1e-10
+    else:
+        # refinement stops on the FP64 residual of the given Phi, which may
+        # sit just above tol: at most one short refinement step
+        assert rel(host(phi), ref) <= 1e-8
+    x5, _, _ = g.pcg(g.rhs(br), 1e-300, maxit=5)
+    phi = dev(x5)
+    if prec == "mixed":
+        plan.solve_mixed(dev(br), 1e-12, phi)
+    else:
+        plan.solve(dev(br), 1e-12, phi)
+    assert rel(host(phi), ref) <= (1e-9 if prec == "fp64" else 1e-8)
+    plan.close()
